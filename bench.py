@@ -1,0 +1,420 @@
+"""Benchmark: multiple-precision CSR SpMV throughput (Gnnz/s) on GB300.
+
+Workload (one step): y = A x in DD, TD and QD (P mode, binary64 values
+promoted) on two real matrices shaped like the paper's SpMV workloads
+(arXiv 2412.17510, Section 4.1, SuiteSparse stand-ins):
+  (a) 3D 27-point stencil on a 128^3 grid, non-periodic (n = 2,097,152,
+      nnz = 55,742,968), off-diagonals N(0,1), diagonal = row |sum| + 1;
+  (b) power-law rows, n = 1,000,000, lengths Zipf(1.5) clipped to [1, 20000]
+      (nnz ~ 2.17e8), uniform distinct columns, N(0,1) values;
+x with every component random, seed 0.  value = (sum of nnz over the six
+products) / (device time of the step).  Inputs are resident in HBM; the L2
+cache is flushed (a 512 MiB write) between timed steps, outside the timed
+events.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+N > 1 runs under torch.distributed.run; every rank multiplies its own copy of
+the workload (independent problems, no collective on the data path), the time
+is the maximum over ranks and value counts the nnz of all ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "MP-SpMV Gnnz/s (DD/TD/QD, real/cplx), % roofline; CG time-to-1e-30 vs plain"
+UNIT = "Gnnz/s"
+PRECS = (2, 3, 4)
+PNAME = {1: "D", 2: "DD", 3: "TD", 4: "QD"}
+# binary64 operations per stored entry: one MP multiply + one MP add
+# (Algorithms 2 + 1 for DD; QD sloppy mul + add; TD = QD with zero fourth
+# components plus one folding addition each) -- the oracle's operation counts.
+OPS_PER_ENTRY = {2: 9 + 11, 3: 124 + 88, 4: 123 + 87}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def make_matrices(small=False):
+    if small:
+        return {"stencil27_32^3": workloads.stencil_27pt(32), "powerlaw_1e5": workloads.power_law(100000)}
+    return {"stencil27_128^3": workloads.stencil_27pt(128), "powerlaw_1e6_zipf1.5": workloads.power_law(1000000)}
+
+
+def algorithmic_bytes(nnz, nrows, ncols, L):
+    """Compulsory HBM traffic of one SpMV: per entry a 4-byte column index and
+    L value components; per row its start offset and the L result components;
+    x read once (L components per column)."""
+    return nnz * (4 + 8 * L) + nrows * (8 + 8 * L) + ncols * 8 * L
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ("spmv.cu", "mp_arith.cuh"):
+        with open(os.path.join(ROOT, "paper_2412_17510_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(variant):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "spmv_dram_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("kernel_sha") != kernel_sha():
+        return None
+    v = d.get("variants", {}).get(variant)
+    return v.get("bytes_per_launch") if v else None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (bounded sample, all host cores)
+# ---------------------------------------------------------------------------
+def _oracle_worker(args):
+    indptr, indices, data, x, L = args
+    import oracle as orc
+    A = orc.CSR(len(indptr) - 1, x.shape[1], indptr, indices, data, L, False)
+    t = time.perf_counter()
+    orc.spmv(A, x)
+    return time.perf_counter() - t
+
+
+def _task(ip, a, b, coo, x, L):
+    """Rows a..b-1 as a small CSR over the columns they reference (x gathered
+    and the column indices renumbered, so that only that part of x is sent to
+    the worker)."""
+    lo, hi = ip[a], ip[b]
+    cols = coo.col[lo:hi]
+    uniq, local = np.unique(cols, return_inverse=True)
+    data = np.zeros((L, hi - lo))
+    data[0] = coo.val[0, lo:hi]
+    return (ip[a:b + 1] - lo, local.astype(np.int32), data, np.ascontiguousarray(x[:, uniq]), L)
+
+
+def oracle_sample(mats, xs, entries_per_variant, pool, ncores):
+    """Oracle throughput on a sample: for every (matrix, precision) a block of
+    consecutive rows holding about entries_per_variant entries, cut into
+    ncores slices run in parallel.  xs[matrix][L] is the vector.  Returns
+    per-variant entries/s."""
+    rates = {}
+    for mname, coo in mats.items():
+        ip = np.zeros(coo.nrows + 1, dtype=np.int64)
+        np.add.at(ip, coo.row + 1, 1)
+        ip = np.cumsum(ip)
+        for L in PRECS:
+            want = entries_per_variant[L]
+            r0 = coo.nrows // 3
+            r1 = int(np.searchsorted(ip, ip[r0] + want))
+            r1 = max(r0 + 1, min(r1, coo.nrows))
+            bounds = np.linspace(r0, r1, ncores + 1).astype(np.int64)
+            tasks = [_task(ip, a, b, coo, xs[mname][L], L) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+            # the slices run concurrently: the sample's time is the slowest one
+            dt = max(pool.map(_oracle_worker, tasks, chunksize=1))
+            rates[(mname, L)] = (ip[r1] - ip[r0]) / dt
+    return rates
+
+
+def cpu_rate_for_step(rates, nnz_of):
+    """Aggregate oracle rate over a step with the GPU step's mix of variants."""
+    tot_nnz = sum(nnz_of[v] for v in rates)
+    tot_t = sum(nnz_of[v] / rates[v] for v in rates)
+    return tot_nnz / tot_t
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle timed as it stands
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    mats = make_matrices(args.small)
+    xs = {m: {L: workloads.full_limb_vector(c.ncols, L, seed=0) for L in PRECS} for m, c in mats.items()}
+    nnz_of = {(m, L): c.nnz for m, c in mats.items() for L in PRECS}
+    sample = {2: 400000, 3: 60000, 4: 60000}
+    step_rates = []
+    with ctx.Pool(ncores) as pool:
+        for it in range(args.warmup + args.steps):
+            rates = oracle_sample(mats, xs, sample, pool, ncores)
+            if it >= args.warmup:
+                step_rates.append(cpu_rate_for_step(rates, nnz_of))
+    total_nnz = sum(nnz_of.values())
+    ms = [total_nnz / r * 1e3 for r in step_rates]
+    value = total_nnz / (sum(ms) / len(ms) * 1e-3) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block(mats),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": "per step and per (matrix, precision) a block of consecutive rows holding "
+                                   "%s entries, split over %d processes; time scaled to the full step" %
+                                   (sample, ncores)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_block(mats):
+    return {"workload": "real CSR SpMV, DD/TD/QD P mode: " + ", ".join(
+        "%s (n=%d, nnz=%d)" % (k, v.nrows, v.nnz) for k, v in mats.items()),
+        "x": "every component random, seed 0", "l2": "flushed between timed steps (512 MiB write)",
+        "precisions": [PNAME[L] for L in PRECS]}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--small", action="store_true", help="reduced matrices (development)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    pool = None
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # spawn the oracle workers before the first GPU call
+        pool = mp.get_context("spawn").Pool(ncores)
+
+    import torch
+    import paper_2412_17510_gb300 as mps
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    mats = make_matrices(args.small)
+    variants = []
+    xs_host = {}
+    for mname, coo in mats.items():
+        xs_host[mname] = {L: workloads.full_limb_vector(coo.ncols, L, seed=0) for L in PRECS}
+        for L in PRECS:
+            h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, 0, val_limbs=1)
+            info = mps.mpspmv_get_info(h)
+            x = torch.from_numpy(xs_host[mname][L]).cuda()
+            y = torch.empty((L, coo.nrows), dtype=torch.float64, device="cuda")
+            variants.append(dict(name="%s/%s" % (mname, PNAME[L]), m=mname, L=L, h=h, x=x, y=y, info=info,
+                                 nnz=info["nnz"], nrows=coo.nrows, ncols=coo.ncols))
+    torch.cuda.synchronize()
+
+    fp64_fma = mps.mpspmv_probe_fp64(0)
+    fp64_add = mps.mpspmv_probe_fp64(1)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        for i, v in enumerate(variants):
+            if evs:
+                evs[i][0].record(stream)
+            mps.mpspmv_spmv(v["h"], v["x"], v["y"], stream)
+            if evs:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    all_evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in variants]
+        step(evs)
+        all_evs.append(evs)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+
+    per_var = np.zeros(len(variants))
+    step_ms = []
+    for evs in all_evs:
+        t = [a.elapsed_time(b) for a, b in evs]
+        per_var += np.array(t)
+        step_ms.append(sum(t))
+    per_var /= args.steps
+    ms = float(np.mean(step_ms))
+    if dist:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    step_nnz = sum(v["nnz"] for v in variants)
+    value = step_nnz * world / (ms * 1e-3) / 1e9
+    launches_per_step = sum(1 + (v["info"]["nsplit_rows"] > 0) for v in variants)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e_ms = []
+    h2d = d2h = 0
+    hosts = []
+    for v in variants:
+        xh = torch.from_numpy(xs_host[v["m"]][v["L"]]).pin_memory()
+        yh = torch.empty((v["L"], v["nrows"]), dtype=torch.float64).pin_memory()
+        hosts.append((xh, yh))
+        h2d += xh.numel() * 8
+        d2h += yh.numel() * 8
+    for it in range(max(3, min(args.steps, 10)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for v, (xh, yh) in zip(variants, hosts):
+            mps.mpspmv_spmv_host(v["h"], xh, yh, stream)
+        t1 = time.perf_counter()
+        if it > 0:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e_value = step_nnz * world / (np.mean(e2e_ms) * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (largest share of the step)
+    dom = int(np.argmax(per_var))
+    v = variants[dom]
+    t_s = per_var[dom] * 1e-3
+    ops = v["nnz"] * OPS_PER_ENTRY[v["L"]]
+    byts = algorithmic_bytes(v["nnz"], v["nrows"], v["ncols"], v["L"])
+    hbm = 6786.2
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    t_alu = ops / fp64_fma
+    t_hbm = byts / (hbm * 1e9)
+    bound = "alu" if t_alu >= t_hbm else "hbm"
+    if bound == "alu":
+        achieved, peak, unit = ops / t_s / 1e12, fp64_fma / 1e12, "T binary64 instr/s"
+    else:
+        achieved, peak, unit = byts / t_s / 1e9, hbm, "GB/s"
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": stored_traffic(v["name"]), "kernel": "spmv_runs_kernel + combine_kernel, " + v["name"],
+            "peak_source": "measured in this run by mpspmv_probe_fp64 (DFMA chains, all SMs)"
+            if bound == "alu" else "MEASURED_PEAKS.json hbm_gbs",
+            "algorithmic_ops_per_launch": ops, "algorithmic_bytes_per_launch": byts,
+            "fp64_dadd_peak_tinstr_s": fp64_add / 1e12}
+
+    breakdown = {}
+    for i, w in enumerate(variants):
+        t = per_var[i] * 1e-3
+        o = w["nnz"] * OPS_PER_ENTRY[w["L"]]
+        b = algorithmic_bytes(w["nnz"], w["nrows"], w["ncols"], w["L"])
+        troof = max(o / fp64_fma, b / (hbm * 1e9))
+        breakdown[w["name"]] = {"ms": per_var[i], "gnnz_s": w["nnz"] / t / 1e9, "roofline_frac": troof / t,
+                                "fp64_tinstr_s": o / t / 1e12, "hbm_gbs": b / t / 1e9, "chunk": w["info"]["chunk"]}
+
+    cpu = None
+    if pool is not None:
+        nnz_of = {(w["m"], w["L"]): w["nnz"] for w in variants}
+        sample = {2: 4000000, 3: 500000, 4: 500000}
+        t0 = time.perf_counter()
+        rates = oracle_sample(mats, xs_host, sample, pool, ncores)
+        cpu = {"value": cpu_rate_for_step(rates, nnz_of) / 1e9, "unit": UNIT, "cores": ncores, "kind": "oracle",
+               "sample": "per (matrix, precision) a block of consecutive rows holding %s entries (DD/TD/QD), split "
+                         "over %d spawned processes; rates combined with the GPU step's mix" % (sample, ncores),
+               "wall_s": time.perf_counter() - t0}
+        pool.close()
+
+    for w in variants:
+        mps.mpspmv_destroy(w["h"])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_block(mats),
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "fp64_peak_tinstr_s": {"dfma": fp64_fma / 1e12, "dadd": fp64_add / 1e12},
+            "breakdown": breakdown,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

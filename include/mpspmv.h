@@ -1,0 +1,160 @@
+/*
+ * mpspmv.h -- C ABI of the GB300 (sm_103a) multiple-precision sparse library.
+ *
+ * Multiple-precision CSR sparse matrix-vector products y = A x in
+ * double-double (DD), triple-double (TD) and quad-double (QD) arithmetic for
+ * real and complex A (arXiv 2412.17510, Kouya: Sections 2 and 3), the
+ * multi-right-hand-side form Y = A X, and the CG / BiCGSTAB loops built on
+ * them (Section 4.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A number with L components (L = 1 binary64, 2 DD, 3 TD, 4 QD) is the
+ *    unevaluated sum of L binary64 values, leading component first.
+ *  - Structure of limbs (Section 3: "allocated independently as binary64
+ *    matrices and vectors for each component"): a vector of length n is P
+ *    consecutive planes of n binary64 values, plane p holding component p.
+ *    Real data: P = L.  Complex data (Eq. complex_expression): P = 2L, planes
+ *    0..L-1 the real part's components, planes L..2L-1 the imaginary part's.
+ *  - Device pointers are CUDA device addresses on the device that was
+ *    current when the handle was created; "host" pointers are ordinary (or
+ *    pinned) host memory.  Pointers may not alias unless stated.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it and returns before completion unless
+ *    stated.
+ *  - Every function returns an int status: MPSPMV_OK (0) or a negative code
+ *    below.  No exception or CUDA error crosses the ABI; on error the outputs
+ *    are unspecified unless stated and the handle stays valid.
+ */
+#ifndef MPSPMV_H
+#define MPSPMV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define MPSPMV_OK 0
+#define MPSPMV_EINVAL (-1)     /* bad argument: size, index, precision, flag, NULL, NaN/Inf input */
+#define MPSPMV_ENOMEM (-2)     /* device or host allocation failed */
+#define MPSPMV_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed */
+#define MPSPMV_ENOTSUP (-4)    /* combination of options not supported */
+#define MPSPMV_EBREAKDOWN (-5) /* Krylov breakdown: zero or non-finite scalar */
+#define MPSPMV_ENOCONV (-6)    /* maxit reached before the stopping test held */
+#define MPSPMV_ETIMEOUT (-7)   /* a bounded device-side wait expired */
+
+/* Precision tag = number of binary64 components L. */
+typedef enum { MPSPMV_D = 1, MPSPMV_DD = 2, MPSPMV_TD = 3, MPSPMV_QD = 4 } mpspmv_prec;
+
+/* Flags for mpspmv_create_csr. */
+#define MPSPMV_COMPLEX 1u   /* A and the vectors are complex (P = 2L planes) */
+#define MPSPMV_MIXED 2u     /* "M" mode (Section 4): A kept in binary64, products MP x binary64
+                               (Algorithms 3-5); requires val_limbs == 1 */
+#define MPSPMV_SYMMETRIC 4u /* triplets hold one triangle (Matrix Market "symmetric"):
+                               every off-diagonal (i,j,v) also stands for (j,i,v) */
+#define MPSPMV_ONE_BASED 8u /* row/col indices start at 1 (Matrix Market) */
+
+typedef struct mpspmv_mat* mpspmv_h;
+
+/* Read-only description of a handle. */
+typedef struct {
+  int64_t nrows, ncols;
+  int64_t nnz;          /* stored entries after duplicate merging (and symmetric expansion) */
+  int64_t max_row_nnz;  /* longest row: the m of the error bound */
+  int64_t nchunks;      /* fixed-size runs of stored entries, one per thread */
+  int64_t nsplit_rows;  /* rows whose entries span more than one run */
+  int32_t prec;         /* L */
+  int32_t planes;       /* P = L or 2L */
+  int32_t chunk;        /* entries per run (K) */
+  uint32_t flags;
+  int64_t device_bytes; /* device memory owned by the handle */
+} mpspmv_info;
+
+/*
+ * mpspmv_create_csr -- build a device CSR matrix from COO / Matrix Market
+ * triplets (Section 3: the COO arrays data/row/col and the CSR arrays
+ * data/indices/indptr of the worked 5x5 example).
+ *
+ *  out        receives the new handle (owned by the caller; release with
+ *             mpspmv_destroy).
+ *  nrows, ncols, nnz   matrix shape and number of triplets (nnz may be 0).
+ *  row, col   host arrays of nnz indices, any order; 0-based unless
+ *             MPSPMV_ONE_BASED.  Indices outside the shape -> MPSPMV_EINVAL.
+ *  val        host values, structure of limbs: val_limbs planes of nnz
+ *             (2*val_limbs planes if MPSPMV_COMPLEX: real components, then
+ *             imaginary components).  Components beyond val_limbs are zero
+ *             ("P" mode promotes binary64 data with zero lower components).
+ *             NaN or Inf -> MPSPMV_EINVAL.
+ *  val_limbs  1..prec (exactly 1 with MPSPMV_MIXED).
+ *  prec       MPSPMV_DD, MPSPMV_TD or MPSPMV_QD (MPSPMV_D: binary64).
+ *  flags      MPSPMV_COMPLEX | MPSPMV_MIXED | MPSPMV_SYMMETRIC | MPSPMV_ONE_BASED.
+ *  stream     stream for the uploads and the device-side build.
+ *
+ * Triplets are ordered by (row, col); duplicates are summed in the working
+ * precision in input order.  The library copies what it needs: the caller
+ * may free row/col/val when the call returns (it synchronises `stream`).
+ */
+int mpspmv_create_csr(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz, const int64_t* row,
+                      const int64_t* col, const double* val, int val_limbs, int prec, unsigned flags,
+                      void* stream);
+
+/* Release a handle and all device memory it owns (synchronises the device). */
+int mpspmv_destroy(mpspmv_h h);
+
+/* Static description of a status code (never NULL). */
+const char* mpspmv_strerror(int status);
+
+/* Fill *info (host struct) for handle h. */
+int mpspmv_get_info(mpspmv_h h, mpspmv_info* info);
+
+/*
+ * mpspmv_spmv -- y = A x in the handle's precision (Section 3; complex by
+ * Eq. complex_spmv: re = A_re x_re - A_im x_im, im = A_re x_im + A_im x_re).
+ *
+ *  x  device, P planes of ncols (read only).
+ *  y  device, P planes of nrows (overwritten; must not overlap x).
+ *
+ * Each stored entry contributes one MP product and one MP addition
+ * (Algorithms 2 and 1 for DD; the QD / TD sloppy forms for QD / TD).  The
+ * result satisfies |y_i - (Ax)_i| <= 8 m u (|A||x|)_i componentwise, with m
+ * the longest row and u = 2^-104, 2^-155, 2^-207 (DD, TD, QD).  Asynchronous.
+ */
+int mpspmv_spmv(mpspmv_h h, const double* x, double* y, void* stream);
+
+/*
+ * mpspmv_spmv_host -- mpspmv_spmv with host buffers: copies x (P planes of
+ * ncols) to device memory owned by the handle, multiplies, copies y (P planes
+ * of nrows) back and synchronises `stream` before returning.
+ */
+int mpspmv_spmv_host(mpspmv_h h, const double* x_host, double* y_host, void* stream);
+
+/*
+ * mpspmv_spmm -- Y = A X for k right-hand sides (1 <= k <= 32).
+ *
+ *  X  device, P planes; plane p, row j, column c at X[(p*ncols + j)*ldx + c]
+ *     (right-hand sides contiguous, so one stored entry of A serves all k).
+ *  Y  device, same layout with nrows and ldy.  ldx, ldy >= k.
+ * Column c of Y equals mpspmv_spmv applied to column c of X.  Asynchronous.
+ */
+int mpspmv_spmm(mpspmv_h h, int k, const double* X, int64_t ldx, double* Y, int64_t ldy, void* stream);
+
+/*
+ * mpspmv_probe_fp64 -- measured binary64 instruction throughput of this GPU
+ * at the current clocks (the compute denominator of the SpMV roofline; the
+ * paper has no counterpart -- its kernels are CPU SIMD code).
+ *
+ *  op           0 = DFMA, 1 = DADD, 2 = DMUL.
+ *  iters        loop trips per thread (each trip = 8 independent instructions).
+ *  instr_per_s  host; receives the best of two timed runs, in instructions/s.
+ * Synchronous: allocates a small scratch buffer and synchronises `stream`.
+ */
+int mpspmv_probe_fp64(int op, int iters, double* instr_per_s, void* stream);
+
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPSPMV_H */

@@ -1,0 +1,159 @@
+"""Python binding of ``libmpspmv.so`` (C ABI in ``include/mpspmv.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions keep the C names; device arrays are passed as torch CUDA
+tensors (or raw integer addresses), host arrays as numpy arrays, streams as
+``torch.cuda.Stream`` objects (or raw handles).  A non-zero status raises
+``MpspmvError``.  Importing this package fails loudly when the compiled
+library is missing: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpspmv.so")
+
+MPSPMV_OK = 0
+MPSPMV_EINVAL = -1
+MPSPMV_ENOMEM = -2
+MPSPMV_ECUDA = -3
+MPSPMV_ENOTSUP = -4
+MPSPMV_EBREAKDOWN = -5
+MPSPMV_ENOCONV = -6
+MPSPMV_ETIMEOUT = -7
+
+MPSPMV_D, MPSPMV_DD, MPSPMV_TD, MPSPMV_QD = 1, 2, 3, 4
+MPSPMV_COMPLEX, MPSPMV_MIXED, MPSPMV_SYMMETRIC, MPSPMV_ONE_BASED = 1, 2, 4, 8
+
+PREC = {"d": 1, "dd": 2, "td": 3, "qd": 4}
+
+
+class MpspmvError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, strerror(status), status))
+
+
+class mpspmv_info(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("max_row_nnz", ctypes.c_int64), ("nchunks", ctypes.c_int64), ("nsplit_rows", ctypes.c_int64),
+                ("prec", ctypes.c_int32), ("planes", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("device_bytes", ctypes.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmpspmv.so is not built (run __graft_entry__.build() or "
+                          "python paper_2412_17510_gb300/build.py)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    sigs = {
+        "mpspmv_create_csr": [ctypes.POINTER(vp), i64, i64, i64, vp, vp, vp, c_int, c_int, ctypes.c_uint, vp],
+        "mpspmv_destroy": [vp],
+        "mpspmv_get_info": [vp, ctypes.POINTER(mpspmv_info)],
+        "mpspmv_spmv": [vp, vp, vp, vp],
+        "mpspmv_spmv_host": [vp, vp, vp, vp],
+        "mpspmv_spmm": [vp, c_int, vp, i64, vp, i64, vp],
+        "mpspmv_probe_fp64": [c_int, c_int, ctypes.POINTER(ctypes.c_double), vp],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = c_int
+    lib.mpspmv_strerror.argtypes = [c_int]
+    lib.mpspmv_strerror.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def _ptr(a):
+    """Address of a torch tensor / numpy array / integer."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(a))
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st, where):
+    if st != MPSPMV_OK:
+        raise MpspmvError(st, where)
+
+
+def strerror(status):
+    return _lib.mpspmv_strerror(status).decode()
+
+
+def mpspmv_create_csr(nrows, ncols, row, col, val, prec, flags=0, val_limbs=None, stream=None):
+    """Create a handle from host COO triplets.  ``val`` is a float64 array of
+    shape (val_limbs * V, nnz), V = 2 for complex.  Returns the handle."""
+    row = np.ascontiguousarray(row, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int64)
+    val = np.ascontiguousarray(np.atleast_2d(val), dtype=np.float64)
+    nnz = row.shape[0]
+    V = 2 if flags & MPSPMV_COMPLEX else 1
+    if val_limbs is None:
+        val_limbs = val.shape[0] // V
+    if col.shape[0] != nnz or val.shape != (val_limbs * V, nnz):
+        raise ValueError("triplet arrays disagree in length or value planes")
+    h = ctypes.c_void_p()
+    st = _lib.mpspmv_create_csr(ctypes.byref(h), nrows, ncols, nnz, row.ctypes.data, col.ctypes.data,
+                                val.ctypes.data, val_limbs, prec, flags, _stream(stream))
+    _check(st, "mpspmv_create_csr")
+    return h
+
+
+def mpspmv_destroy(h):
+    _check(_lib.mpspmv_destroy(h), "mpspmv_destroy")
+
+
+def mpspmv_get_info(h):
+    info = mpspmv_info()
+    _check(_lib.mpspmv_get_info(h, ctypes.byref(info)), "mpspmv_get_info")
+    return {k: getattr(info, k) for k, _ in mpspmv_info._fields_}
+
+
+def mpspmv_spmv(h, x, y, stream=None):
+    _check(_lib.mpspmv_spmv(h, _ptr(x), _ptr(y), _stream(stream)), "mpspmv_spmv")
+
+
+def mpspmv_spmv_host(h, x_host, y_host, stream=None):
+    _check(_lib.mpspmv_spmv_host(h, _ptr(x_host), _ptr(y_host), _stream(stream)), "mpspmv_spmv_host")
+
+
+def mpspmv_spmm(h, k, X, ldx, Y, ldy, stream=None):
+    _check(_lib.mpspmv_spmm(h, k, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)), "mpspmv_spmm")
+
+
+def mpspmv_probe_fp64(op, iters=4096, stream=None):
+    """Measured binary64 instructions per second (op 0 DFMA, 1 DADD, 2 DMUL)."""
+    r = ctypes.c_double()
+    _check(_lib.mpspmv_probe_fp64(op, iters, ctypes.byref(r), _stream(stream)), "mpspmv_probe_fp64")
+    return r.value
+
+
+def library():
+    """The loaded ctypes library (for symbol checks)."""
+    return _lib

@@ -1,0 +1,75 @@
+// internal.h -- handle layout and launch helpers shared by the library's
+// translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mpspmv.h"
+
+#define MPS_CUDA(call)                              \
+  do {                                              \
+    cudaError_t _e = (call);                        \
+    if (_e != cudaSuccess) {                        \
+      mps_note_cuda_error(_e, #call, __FILE__, __LINE__); \
+      return MPSPMV_ECUDA;                          \
+    }                                               \
+  } while (0)
+
+void mps_note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Device view of a matrix, passed to kernels by value.
+//
+// Stored entries are cut into runs ("chunks") of K consecutive entries in
+// CSR order; chunk c is summed by one thread.  Runs are grouped 32 at a time
+// into tiles whose entries are stored transposed (entry j of the chunk in
+// lane l of tile t sits at t*32*K + j*32 + l), so the 32 threads of a warp
+// read 32 consecutive values per step.  Every value plane and the column
+// array use this tiled order; tlen is the padded length of one plane.
+struct DevMat {
+  int64_t nrows, ncols, nnz, nchunks, tlen;
+  int32_t K;
+  const int64_t* indptr;    // nrows + 1, CSR row starts (in entry order)
+  const int32_t* cols;      // tlen, tiled
+  const double* vals;       // Pv planes of tlen, tiled
+  const int64_t* chunk_row; // nchunks: the row holding entry c*K
+  const int64_t* split_rows;// rows whose entries span > 1 chunk
+  int64_t nsplit;
+};
+
+struct mpspmv_mat {
+  int device;
+  int L, P, Pv;  // components, vector planes, stored value planes
+  bool cplx, mixed;
+  unsigned flags;
+  int64_t nrows, ncols, nnz, max_row_nnz;
+  int32_t K;
+  int64_t nchunks, ntiles, tlen, nsplit;
+  int64_t* d_indptr = nullptr;
+  int32_t* d_cols = nullptr;
+  double* d_vals = nullptr;
+  int64_t* d_chunk_row = nullptr;
+  int64_t* d_split = nullptr;
+  double* d_carry = nullptr;      // 2 * P * nchunks * carry_k
+  int carry_k = 0;                // right-hand sides the carry buffer holds
+  double* d_xbuf = nullptr;       // host-buffer entry points
+  double* d_ybuf = nullptr;
+  int64_t device_bytes = 0;
+
+  DevMat view() const {
+    DevMat m;
+    m.nrows = nrows; m.ncols = ncols; m.nnz = nnz; m.nchunks = nchunks; m.tlen = tlen; m.K = K;
+    m.indptr = d_indptr; m.cols = d_cols; m.vals = d_vals; m.chunk_row = d_chunk_row;
+    m.split_rows = d_split; m.nsplit = nsplit;
+    return m;
+  }
+};
+
+// Launchers implemented in spmv.cu
+int mps_build_tiles(mpspmv_mat* h, const double* d_sorted_vals, int64_t nin, int vin_limbs,
+                    const int64_t* d_run_start, const int64_t* d_unique_cols_src, cudaStream_t s);
+int mps_launch_spmv(const mpspmv_mat* h, const double* x, double* y, cudaStream_t s);
+int mps_launch_spmm(mpspmv_mat* h, int k, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                    cudaStream_t s);
+int mps_ensure_carry(mpspmv_mat* h, int k);
+
+static inline cudaStream_t mps_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }

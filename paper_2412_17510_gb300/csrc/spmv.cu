@@ -1,0 +1,318 @@
+// spmv.cu -- multiple-precision CSR SpMV / SpMM on the binary64 pipe
+// (arXiv 2412.17510, Section 3; complex by Eq. complex_spmv).
+//
+// Work decomposition (GB300 design, not the paper's AVX2 one): the stored
+// entries are cut into runs of K consecutive entries and each thread sums one
+// run, left to right, with one MP multiply and one MP add per entry -- the
+// same operation sequence as a sequential row sweep.  Every thread therefore
+// issues the same binary64 instruction stream (K products and K additions),
+// whatever the row lengths: short rows, 27-entry stencil rows and
+// 20,000-entry power-law rows all keep the FP64 pipe equally busy.  A row
+// that ends inside a run is written directly; a row cut by a run boundary
+// leaves a partial sum per run in a carry buffer, and a second kernel adds
+// the partials of each such row in run order.
+//
+// Rows that lie inside one run are therefore computed exactly as a
+// sequential sweep computes them (bit-identical), and rows cut by run
+// boundaries differ only in the association of the partial sums.
+#include <algorithm>
+
+#include "internal.h"
+#include "mp_arith.cuh"
+
+using namespace mpk;
+
+namespace {
+
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ int64_t tile_pos(int64_t c, int j, int K) {
+  return (c >> 5) * (32 * (int64_t)K) + (int64_t)j * 32 + (c & 31);
+}
+
+// ---------------------------------------------------------------------------
+// Build: sorted triplets (duplicates adjacent) -> tiled column / value arrays.
+// ---------------------------------------------------------------------------
+template <int L, bool CPLX, bool MIXED>
+__global__ void build_tiles_kernel(DevMat m, int32_t* __restrict__ cols_out, double* __restrict__ vals_out,
+                                   const double* __restrict__ vin, int64_t nin, int vin_limbs,
+                                   const int64_t* __restrict__ run_start, const int64_t* __restrict__ col_src) {
+  int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= m.nnz) return;
+  const int64_t t0 = run_start ? run_start[u] : u;
+  const int64_t t1 = run_start ? run_start[u + 1] : u + 1;
+  const int64_t c = u / m.K;
+  const int j = (int)(u - c * m.K);
+  const int64_t pos = tile_pos(c, j, m.K);
+  cols_out[pos] = (int32_t)col_src[t0];
+  constexpr int NC = CPLX ? 2 : 1;
+#pragma unroll
+  for (int part = 0; part < NC; part++) {
+    if (MIXED) {
+      double acc = vin[(int64_t)part * nin + t0];
+      for (int64_t t = t0 + 1; t < t1; t++) acc = __dadd_rn(acc, vin[(int64_t)part * nin + t]);
+      vals_out[(int64_t)part * m.tlen + pos] = acc;
+    } else {
+      mp<L> acc;
+#pragma unroll
+      for (int l = 0; l < L; l++) acc.v[l] = l < vin_limbs ? vin[(int64_t)(part * vin_limbs + l) * nin + t0] : 0.0;
+      for (int64_t t = t0 + 1; t < t1; t++) {
+        mp<L> v;
+#pragma unroll
+        for (int l = 0; l < L; l++) v.v[l] = l < vin_limbs ? vin[(int64_t)(part * vin_limbs + l) * nin + t] : 0.0;
+        acc = mp_add<L>(acc, v);
+      }
+#pragma unroll
+      for (int l = 0; l < L; l++) vals_out[(int64_t)(part * L + l) * m.tlen + pos] = acc.v[l];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-entry contribution: (sr, si) += a * x[col]  (Eq. complex_spmv order:
+// re += a_re x_re; re += -(a_im x_im); im += a_re x_im; im += a_im x_re).
+// ---------------------------------------------------------------------------
+template <int L, bool CPLX, bool MIXED>
+__device__ __forceinline__ void accumulate(const DevMat& m, int64_t pos, const double* __restrict__ x,
+                                           int64_t xs, int64_t xcol_off, mp<L>& sr, mp<L>& si) {
+  const int64_t col = __ldg(m.cols + pos);
+  mp<L> xr, xi;
+#pragma unroll
+  for (int l = 0; l < L; l++) xr.v[l] = __ldg(x + (int64_t)l * xs + col * xcol_off);
+  if (CPLX) {
+#pragma unroll
+    for (int l = 0; l < L; l++) xi.v[l] = __ldg(x + (int64_t)(L + l) * xs + col * xcol_off);
+  }
+  if (MIXED) {
+    const double ar = __ldg(m.vals + pos);
+    sr = mp_add<L>(sr, mp_mul_d<L>(xr, ar));
+    if (CPLX) {
+      const double ai = __ldg(m.vals + m.tlen + pos);
+      sr = mp_add<L>(sr, mp_neg<L>(mp_mul_d<L>(xi, ai)));
+      si = mp_add<L>(si, mp_mul_d<L>(xi, ar));
+      si = mp_add<L>(si, mp_mul_d<L>(xr, ai));
+    }
+  } else {
+    mp<L> ar;
+#pragma unroll
+    for (int l = 0; l < L; l++) ar.v[l] = __ldg(m.vals + (int64_t)l * m.tlen + pos);
+    sr = mp_add<L>(sr, mp_mul<L>(ar, xr));
+    if (CPLX) {
+      mp<L> ai;
+#pragma unroll
+      for (int l = 0; l < L; l++) ai.v[l] = __ldg(m.vals + (int64_t)(L + l) * m.tlen + pos);
+      sr = mp_add<L>(sr, mp_neg<L>(mp_mul<L>(ai, xi)));
+      si = mp_add<L>(si, mp_mul<L>(ar, xi));
+      si = mp_add<L>(si, mp_mul<L>(ai, xr));
+    }
+  }
+}
+
+template <int L, bool CPLX>
+__device__ __forceinline__ void store_mp(double* __restrict__ out, int64_t ps, int64_t idx, const mp<L>& sr,
+                                         const mp<L>& si) {
+#pragma unroll
+  for (int l = 0; l < L; l++) out[(int64_t)l * ps + idx] = sr.v[l];
+  if (CPLX) {
+#pragma unroll
+    for (int l = 0; l < L; l++) out[(int64_t)(L + l) * ps + idx] = si.v[l];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Run kernel.  Vectors: x plane stride xs, entry j at x[j*xoff] within a plane
+// (xoff = ldx for SpMM, 1 for SpMV); y likewise.  rhs selects the column of a
+// multi-right-hand-side product (0 for SpMV); `kp` threads share a run.
+// Carry layout: carry[((w*P + p)*nchunks + c)*kc + rhs], w = 0 first-row
+// partial, w = 1 last-row partial.
+// ---------------------------------------------------------------------------
+template <int L, bool CPLX, bool MIXED>
+__global__ void __launch_bounds__(kThreads) spmv_runs_kernel(DevMat m, const double* __restrict__ x, int64_t xs,
+                                                             int64_t xoff, double* __restrict__ y, int64_t ys,
+                                                             int64_t yoff, double* __restrict__ carry, int kc,
+                                                             int kp, int k) {
+  constexpr int P = CPLX ? 2 * L : L;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t c = t / kp;
+  const int rhs = (int)(t - c * kp);
+  if (c >= m.nchunks || rhs >= k) return;
+  const double* xr = x + rhs;
+  double* yr = y + rhs;
+  const int64_t k0 = c * m.K;
+  const int64_t k1 = min(k0 + (int64_t)m.K, m.nnz);
+  int64_t row = __ldg(m.chunk_row + c);
+  const int64_t first_row = row;
+  const bool first_partial = __ldg(m.indptr + row) < k0;
+  int64_t rend = __ldg(m.indptr + row + 1);
+  const mp<L> z = mp_zero<L>();
+  if (c == 0) {  // rows before the first stored entry are empty
+    for (int64_t r = 0; r < row; r++) store_mp<L, CPLX>(yr, ys, r * yoff, z, z);
+  }
+  mp<L> sr = z, si = z;
+  bool have = false;
+  const int n = (int)(k1 - k0);
+  const int64_t chunk_base = tile_pos(c, 0, m.K);
+  for (int j = 0; j < n; j++) {
+    accumulate<L, CPLX, MIXED>(m, chunk_base + (int64_t)j * 32, xr, xs, xoff, sr, si);
+    have = true;
+    const int64_t kk = k0 + j + 1;
+    if (kk == rend) {
+      if (row == first_row && first_partial) {
+#pragma unroll
+        for (int p = 0; p < P; p++)
+          carry[((int64_t)(0 * P + p) * m.nchunks + c) * kc + rhs] = p < L ? sr.v[p % L] : si.v[p % L];
+      } else {
+        store_mp<L, CPLX>(yr, ys, row * yoff, sr, si);
+      }
+      sr = z;
+      si = z;
+      have = false;
+      row++;
+      while (row < m.nrows && __ldg(m.indptr + row + 1) == kk) {  // empty rows at this position
+        store_mp<L, CPLX>(yr, ys, row * yoff, z, z);
+        row++;
+      }
+      rend = row < m.nrows ? __ldg(m.indptr + row + 1) : INT64_MAX;
+    }
+  }
+  if (have) {
+    const int w = (row == first_row && first_partial) ? 0 : 1;
+#pragma unroll
+    for (int p = 0; p < P; p++)
+      carry[((int64_t)(w * P + p) * m.nchunks + c) * kc + rhs] = p < L ? sr.v[p % L] : si.v[p % L];
+  }
+}
+
+// Rows cut by run boundaries: partial of the run where the row starts (slot
+// w = 1), then the partials of the following runs (slot w = 0) in order.
+template <int L, bool CPLX>
+__global__ void __launch_bounds__(kThreads) combine_kernel(DevMat m, double* __restrict__ y, int64_t ys,
+                                                           int64_t yoff, const double* __restrict__ carry,
+                                                           int kc, int k) {
+  constexpr int P = CPLX ? 2 * L : L;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t s = t / k;
+  const int rhs = (int)(t - s * k);
+  if (s >= m.nsplit) return;
+  const int64_t r = __ldg(m.split_rows + s);
+  const int64_t c0 = __ldg(m.indptr + r) / m.K;
+  const int64_t c1 = (__ldg(m.indptr + r + 1) - 1) / m.K;
+  auto ld = [&](int w, int p, int64_t c) { return carry[((int64_t)(w * P + p) * m.nchunks + c) * kc + rhs]; };
+  mp<L> sr, si;
+#pragma unroll
+  for (int l = 0; l < L; l++) sr.v[l] = ld(1, l, c0);
+  if (CPLX) {
+#pragma unroll
+    for (int l = 0; l < L; l++) si.v[l] = ld(1, L + l, c0);
+  }
+  for (int64_t c = c0 + 1; c <= c1; c++) {
+    mp<L> ar, ai;
+#pragma unroll
+    for (int l = 0; l < L; l++) ar.v[l] = ld(0, l, c);
+    sr = mp_add<L>(sr, ar);
+    if (CPLX) {
+#pragma unroll
+      for (int l = 0; l < L; l++) ai.v[l] = ld(0, L + l, c);
+      si = mp_add<L>(si, ai);
+    }
+  }
+  store_mp<L, CPLX>(y + rhs, ys, r * yoff, sr, si);
+}
+
+template <int L, bool CPLX, bool MIXED>
+int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, double* y, int64_t ys,
+               int64_t yoff, int k, cudaStream_t s) {
+  const DevMat m = h->view();
+  if (h->nnz == 0) {
+    // no stored entry: y = 0
+    for (int p = 0; p < h->P; p++)
+      for (int c = 0; c < k; c++) {
+        if (yoff == 1) {
+          MPS_CUDA(cudaMemsetAsync(y + (int64_t)p * ys, 0, sizeof(double) * h->nrows, s));
+          break;
+        }
+        MPS_CUDA(cudaMemset2DAsync(y + (int64_t)p * ys + c, sizeof(double) * yoff, 0, sizeof(double), h->nrows, s));
+      }
+    return MPSPMV_OK;
+  }
+  int kp = 1;
+  while (kp < k) kp <<= 1;
+  const int64_t threads = h->nchunks * kp;
+  const int64_t blocks = (threads + kThreads - 1) / kThreads;
+  spmv_runs_kernel<L, CPLX, MIXED><<<(unsigned)blocks, kThreads, 0, s>>>(m, x, xs, xoff, y, ys, yoff, h->d_carry,
+                                                                        h->carry_k, kp, k);
+  MPS_CUDA(cudaGetLastError());
+  if (h->nsplit > 0) {
+    const int64_t ct = h->nsplit * k;
+    combine_kernel<L, CPLX><<<(unsigned)((ct + kThreads - 1) / kThreads), kThreads, 0, s>>>(m, y, ys, yoff, h->d_carry,
+                                                                                         h->carry_k, k);
+    MPS_CUDA(cudaGetLastError());
+  }
+  return MPSPMV_OK;
+}
+
+template <int L, bool CPLX, bool MIXED>
+int build_one(mpspmv_mat* h, const double* vin, int64_t nin, int vin_limbs, const int64_t* run_start,
+              const int64_t* col_src, cudaStream_t s) {
+  if (h->nnz == 0) return MPSPMV_OK;
+  const int64_t blocks = (h->nnz + kThreads - 1) / kThreads;
+  build_tiles_kernel<L, CPLX, MIXED><<<(unsigned)blocks, kThreads, 0, s>>>(h->view(), h->d_cols, h->d_vals, vin, nin,
+                                                                          vin_limbs, run_start, col_src);
+  MPS_CUDA(cudaGetLastError());
+  return MPSPMV_OK;
+}
+
+}  // namespace
+
+// Precision / complex / mode dispatch.
+#define MPS_DISPATCH(FN, h, ...)                                                   \
+  do {                                                                            \
+    switch ((h)->L * 4 + ((h)->cplx ? 2 : 0) + ((h)->mixed ? 1 : 0)) {            \
+      case 1 * 4 + 0: return FN<1, false, false>(__VA_ARGS__);                    \
+      case 1 * 4 + 2: return FN<1, true, false>(__VA_ARGS__);                     \
+      case 2 * 4 + 0: return FN<2, false, false>(__VA_ARGS__);                    \
+      case 2 * 4 + 1: return FN<2, false, true>(__VA_ARGS__);                     \
+      case 2 * 4 + 2: return FN<2, true, false>(__VA_ARGS__);                     \
+      case 2 * 4 + 3: return FN<2, true, true>(__VA_ARGS__);                      \
+      case 3 * 4 + 0: return FN<3, false, false>(__VA_ARGS__);                    \
+      case 3 * 4 + 1: return FN<3, false, true>(__VA_ARGS__);                     \
+      case 3 * 4 + 2: return FN<3, true, false>(__VA_ARGS__);                     \
+      case 3 * 4 + 3: return FN<3, true, true>(__VA_ARGS__);                      \
+      case 4 * 4 + 0: return FN<4, false, false>(__VA_ARGS__);                    \
+      case 4 * 4 + 1: return FN<4, false, true>(__VA_ARGS__);                     \
+      case 4 * 4 + 2: return FN<4, true, false>(__VA_ARGS__);                     \
+      case 4 * 4 + 3: return FN<4, true, true>(__VA_ARGS__);                      \
+      default: return MPSPMV_ENOTSUP;                                             \
+    }                                                                             \
+  } while (0)
+
+int mps_build_tiles(mpspmv_mat* h, const double* d_sorted_vals, int64_t nin, int vin_limbs,
+                    const int64_t* d_run_start, const int64_t* d_col_src, cudaStream_t s) {
+  MPS_DISPATCH(build_one, h, h, d_sorted_vals, nin, vin_limbs, d_run_start, d_col_src, s);
+}
+
+int mps_ensure_carry(mpspmv_mat* h, int k) {
+  if (h->carry_k >= k) return MPSPMV_OK;
+  int want = k <= 1 ? 1 : 32;
+  if (h->d_carry) {
+    MPS_CUDA(cudaFree(h->d_carry));
+    h->device_bytes -= (int64_t)sizeof(double) * 2 * h->P * h->nchunks * h->carry_k;
+    h->d_carry = nullptr;
+    h->carry_k = 0;
+  }
+  const int64_t n = 2 * (int64_t)h->P * std::max<int64_t>(h->nchunks, 1) * want;
+  if (cudaMalloc(&h->d_carry, sizeof(double) * n) != cudaSuccess) return MPSPMV_ENOMEM;
+  h->device_bytes += (int64_t)sizeof(double) * n;
+  h->carry_k = want;
+  return MPSPMV_OK;
+}
+
+int mps_launch_spmv(const mpspmv_mat* h, const double* x, double* y, cudaStream_t s) {
+  MPS_DISPATCH(launch_all, h, h, x, h->ncols, 1, y, h->nrows, 1, 1, s);
+}
+
+int mps_launch_spmm(mpspmv_mat* h, int k, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s) {
+  int st = mps_ensure_carry(h, k);
+  if (st != MPSPMV_OK) return st;
+  MPS_DISPATCH(launch_all, h, h, X, h->ncols * ldx, ldx, Y, h->nrows * ldy, ldy, k, s);
+}

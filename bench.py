@@ -242,6 +242,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced matrices (development)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg")
+    ap.add_argument("--only", default=None, help="run one variant, e.g. powerlaw_1e5/QD (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -253,7 +254,7 @@ def main():
     pool = None
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and not args.only:
         # spawn the oracle workers before the first GPU call
         pool = mp.get_context("spawn").Pool(ncores)
 
@@ -272,6 +273,8 @@ def main():
     for mname, coo in mats.items():
         xs_host[mname] = {L: workloads.full_limb_vector(coo.ncols, L, seed=0) for L in PRECS}
         for L in PRECS:
+            if args.only and args.only != "%s/%s" % (mname, PNAME[L]):
+                continue
             h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, 0, val_limbs=1)
             info = mps.mpspmv_get_info(h)
             x = torch.from_numpy(xs_host[mname][L]).cuda()

@@ -141,6 +141,36 @@ int mpspmv_spmv_host(mpspmv_h h, const double* x_host, double* y_host, void* str
 int mpspmv_spmm(mpspmv_h h, int k, const double* X, int64_t ldx, double* Y, int64_t ldy, void* stream);
 
 /*
+ * mpspmv_cg -- conjugate gradients for real symmetric positive definite A
+ * (Section 4.2: CG on nd3k), every vector and scalar in the handle's
+ * precision; unpreconditioned Hestenes-Stiefel form.
+ *
+ *  b       device, L planes of n (right-hand side; n = nrows = ncols).
+ *  x       device, L planes of n: initial guess on entry (the paper uses 0),
+ *          the last iterate on return (also on MPSPMV_ENOCONV).
+ *  rtol, atol  stop when ||r_k||_2 <= rtol ||b||_2 + atol, r_k the recurrence
+ *          residual (the paper: rtol = 1e-13, atol = 1e-99).
+ *  maxit   iteration limit (>= 0).
+ *  iters   host, may be NULL: iterations taken.
+ *  relres  host, may be NULL: ||b - A x||_2 / ||b||_2 of the returned x,
+ *          recomputed in the working precision.
+ * Returns MPSPMV_OK when the test held, MPSPMV_ENOCONV at maxit,
+ * MPSPMV_EBREAKDOWN on a zero or non-finite p'Ap / r'r, MPSPMV_ENOTSUP for a
+ * complex or M-mode handle.  Synchronises `stream` before returning.
+ */
+int mpspmv_cg(mpspmv_h h, const double* b, double* x, double rtol, double atol, int maxit, int* iters,
+              double* relres, void* stream);
+
+/*
+ * mpspmv_bicgstab -- BiCGSTAB (van der Vorst) for real or complex A, r_hat =
+ * r_0, inner products sum conj(u_i) v_i (Section 4.2: product-type Krylov
+ * methods on tub1000).  Arguments and returns as mpspmv_cg; b and x have P
+ * planes (complex: 2L).
+ */
+int mpspmv_bicgstab(mpspmv_h h, const double* b, double* x, double rtol, double atol, int maxit, int* iters,
+                    double* relres, void* stream);
+
+/*
  * mpspmv_probe_fp64 -- measured binary64 instruction throughput of this GPU
  * at the current clocks (the compute denominator of the SpMV roofline; the
  * paper has no counterpart -- its kernels are CPU SIMD code).

@@ -57,6 +57,10 @@ def _load():
         "mpspmv_spmv_host": [vp, vp, vp, vp],
         "mpspmv_spmm": [vp, c_int, vp, i64, vp, i64, vp],
         "mpspmv_probe_fp64": [c_int, c_int, ctypes.POINTER(ctypes.c_double), vp],
+        "mpspmv_cg": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
+                      ctypes.POINTER(ctypes.c_double), vp],
+        "mpspmv_bicgstab": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
+                            ctypes.POINTER(ctypes.c_double), vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -145,6 +149,24 @@ def mpspmv_spmv_host(h, x_host, y_host, stream=None):
 
 def mpspmv_spmm(h, k, X, ldx, Y, ldy, stream=None):
     _check(_lib.mpspmv_spmm(h, k, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)), "mpspmv_spmm")
+
+
+def _solve(fn, name, h, b, x, rtol, atol, maxit, stream, raise_on_noconv):
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    st = fn(h, _ptr(b), _ptr(x), rtol, atol, maxit, ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+    if st not in (MPSPMV_OK, MPSPMV_ENOCONV) or (st == MPSPMV_ENOCONV and raise_on_noconv):
+        raise MpspmvError(st, name)
+    return st, it.value, rr.value
+
+
+def mpspmv_cg(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=False):
+    """CG in place on x.  Returns (status, iterations, true relative residual)."""
+    return _solve(_lib.mpspmv_cg, "mpspmv_cg", h, b, x, rtol, atol, maxit, stream, raise_on_noconv)
+
+
+def mpspmv_bicgstab(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=False):
+    """BiCGSTAB in place on x.  Returns (status, iterations, true relative residual)."""
+    return _solve(_lib.mpspmv_bicgstab, "mpspmv_bicgstab", h, b, x, rtol, atol, maxit, stream, raise_on_noconv)
 
 
 def mpspmv_probe_fp64(op, iters=4096, stream=None):

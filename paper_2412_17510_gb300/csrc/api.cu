@@ -40,6 +40,8 @@ void free_handle(mpspmv_mat* h) {
   cudaFree(h->d_carry);
   cudaFree(h->d_xbuf);
   cudaFree(h->d_ybuf);
+  cudaFree(h->d_kws);
+  cudaFree(h->d_kstate);
   if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
   delete h;
 }

@@ -53,6 +53,9 @@ struct mpspmv_mat {
   int carry_k = 0;                // right-hand sides the carry buffer holds
   double* d_xbuf = nullptr;       // host-buffer entry points
   double* d_ybuf = nullptr;
+  double* d_kws = nullptr;        // Krylov vectors and reduction partials
+  int64_t kws_len = 0;
+  struct KrylovState* d_kstate = nullptr;
   int64_t device_bytes = 0;
 
   DevMat view() const {
@@ -68,6 +71,10 @@ struct mpspmv_mat {
 int mps_build_tiles(mpspmv_mat* h, const double* d_sorted_vals, int64_t nin, int vin_limbs,
                     const int64_t* d_run_start, const int64_t* d_unique_cols_src, cudaStream_t s);
 int mps_launch_spmv(const mpspmv_mat* h, const double* x, double* y, cudaStream_t s);
+// SpMV whose kernels do nothing unless *gate == 0 (device flag, e.g. the
+// status word of a Krylov solver replayed from a CUDA graph).
+int mps_launch_spmv_if_running(const mpspmv_mat* h, const double* x, double* y, const void* gate,
+                               cudaStream_t s);
 int mps_launch_spmm(mpspmv_mat* h, int k, const double* X, int64_t ldx, double* Y, int64_t ldy,
                     cudaStream_t s);
 int mps_ensure_carry(mpspmv_mat* h, int k);

@@ -130,8 +130,9 @@ template <int L, bool CPLX, bool MIXED>
 __global__ void __launch_bounds__(kThreads) spmv_runs_kernel(DevMat m, const double* __restrict__ x, int64_t xs,
                                                              int64_t xoff, double* __restrict__ y, int64_t ys,
                                                              int64_t yoff, double* __restrict__ carry, int kc,
-                                                             int kp, int k) {
+                                                             int kp, int k, const int* __restrict__ gate) {
   constexpr int P = CPLX ? 2 * L : L;
+  if (gate && *gate != 0) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t c = t / kp;
   const int rhs = (int)(t - c * kp);
@@ -188,8 +189,9 @@ __global__ void __launch_bounds__(kThreads) spmv_runs_kernel(DevMat m, const dou
 template <int L, bool CPLX>
 __global__ void __launch_bounds__(kThreads) combine_kernel(DevMat m, double* __restrict__ y, int64_t ys,
                                                            int64_t yoff, const double* __restrict__ carry,
-                                                           int kc, int k) {
+                                                           int kc, int k, const int* __restrict__ gate) {
   constexpr int P = CPLX ? 2 * L : L;
+  if (gate && *gate != 0) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t s = t / k;
   const int rhs = (int)(t - s * k);
@@ -219,10 +221,25 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(DevMat m, double* __r
   store_mp<L, CPLX>(y + rhs, ys, r * yoff, sr, si);
 }
 
+// y = 0 (single right-hand side), gated
+__global__ void zero_kernel(double* y, int64_t ys, int64_t yoff, int64_t nrows, int P, const int* gate) {
+  if (gate && *gate != 0) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nrows * P) return;
+  const int64_t p = t / nrows, r = t - p * nrows;
+  y[p * ys + r * yoff] = 0.0;
+}
+
 template <int L, bool CPLX, bool MIXED>
 int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, double* y, int64_t ys,
-               int64_t yoff, int k, cudaStream_t s) {
+               int64_t yoff, int k, const int* gate, cudaStream_t s) {
   const DevMat m = h->view();
+  if (h->nnz == 0 && gate) {
+    zero_kernel<<<(unsigned)((h->nrows * h->P + kThreads - 1) / kThreads + 1), kThreads, 0, s>>>(y, ys, yoff, h->nrows,
+                                                                                          h->P, gate);
+    MPS_CUDA(cudaGetLastError());
+    return MPSPMV_OK;
+  }
   if (h->nnz == 0) {
     // no stored entry: y = 0
     for (int p = 0; p < h->P; p++)
@@ -240,12 +257,12 @@ int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, d
   const int64_t threads = h->nchunks * kp;
   const int64_t blocks = (threads + kThreads - 1) / kThreads;
   spmv_runs_kernel<L, CPLX, MIXED><<<(unsigned)blocks, kThreads, 0, s>>>(m, x, xs, xoff, y, ys, yoff, h->d_carry,
-                                                                        h->carry_k, kp, k);
+                                                                        h->carry_k, kp, k, gate);
   MPS_CUDA(cudaGetLastError());
   if (h->nsplit > 0) {
     const int64_t ct = h->nsplit * k;
     combine_kernel<L, CPLX><<<(unsigned)((ct + kThreads - 1) / kThreads), kThreads, 0, s>>>(m, y, ys, yoff, h->d_carry,
-                                                                                         h->carry_k, k);
+                                                                                         h->carry_k, k, gate);
     MPS_CUDA(cudaGetLastError());
   }
   return MPSPMV_OK;
@@ -308,11 +325,17 @@ int mps_ensure_carry(mpspmv_mat* h, int k) {
 }
 
 int mps_launch_spmv(const mpspmv_mat* h, const double* x, double* y, cudaStream_t s) {
-  MPS_DISPATCH(launch_all, h, h, x, h->ncols, 1, y, h->nrows, 1, 1, s);
+  MPS_DISPATCH(launch_all, h, h, x, h->ncols, 1, y, h->nrows, 1, 1, nullptr, s);
+}
+
+int mps_launch_spmv_if_running(const mpspmv_mat* h, const double* x, double* y, const void* gate,
+                               cudaStream_t s) {
+  const int* g = static_cast<const int*>(gate);
+  MPS_DISPATCH(launch_all, h, h, x, h->ncols, 1, y, h->nrows, 1, 1, g, s);
 }
 
 int mps_launch_spmm(mpspmv_mat* h, int k, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s) {
   int st = mps_ensure_carry(h, k);
   if (st != MPSPMV_OK) return st;
-  MPS_DISPATCH(launch_all, h, h, X, h->ncols * ldx, ldx, Y, h->nrows * ldy, ldy, k, s);
+  MPS_DISPATCH(launch_all, h, h, X, h->ncols * ldx, ldx, Y, h->nrows * ldy, ldy, k, nullptr, s);
 }

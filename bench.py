@@ -332,7 +332,8 @@ def main():
         ms = float(tt.item())
     step_nnz = sum(v["nnz"] for v in variants)
     value = step_nnz * world / (ms * 1e-3) / 1e9
-    launches_per_step = sum(1 + (v["info"]["nsplit_rows"] > 0) for v in variants)
+    launches_per_step = sum(1 + (v["info"]["nsplit_rows"] > v["info"]["nlong_rows"]) + (v["info"]["nlong_rows"] > 0)
+                            for v in variants)
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e_ms = []

@@ -70,6 +70,7 @@ typedef struct {
   int32_t chunk;        /* entries per run (K) */
   uint32_t flags;
   int64_t device_bytes; /* device memory owned by the handle */
+  int64_t nlong_rows;   /* of nsplit_rows, those spanning more than 32 runs */
 } mpspmv_info;
 
 /*

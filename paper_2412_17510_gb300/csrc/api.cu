@@ -46,12 +46,12 @@ void free_handle(mpspmv_mat* h) {
   delete h;
 }
 
-// Entries per run.  Runs of 16 keep tens of thousands of warps in flight on
-// the matrices of interest; small matrices use shorter runs so that the grid
-// still covers the 152 SMs.
+// Entries per run: the longest of 64, 32, 16, 8, 4 that still leaves about
+// four waves of threads on 152 SMs (768 resident threads each).  Long runs
+// mean fewer rows cut by run boundaries, hence fewer partial sums to combine.
 int32_t pick_chunk(int64_t nnz) {
-  int32_t K = 16;
-  while (K > 4 && nnz / K < 152 * 256) K >>= 1;
+  int32_t K = 64;
+  while (K > 4 && nnz / K < (int64_t)152 * 768 * 4) K >>= 1;
   return K;
 }
 
@@ -184,9 +184,16 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
       chunk_row[c] = r;
     }
   }
-  std::vector<int64_t> split;
-  for (int64_t r = 0; r < nrows; r++)
-    if (indptr[r + 1] > indptr[r] && indptr[r] / K != (indptr[r + 1] - 1) / K) split.push_back(r);
+  // rows cut by run boundaries: short spans first, then the long ones
+  std::vector<int64_t> split, split_long;
+  for (int64_t r = 0; r < nrows; r++) {
+    if (indptr[r + 1] <= indptr[r]) continue;
+    const int64_t span = (indptr[r + 1] - 1) / K - indptr[r] / K;
+    if (span == 0) continue;
+    (span <= kLongSpan ? split : split_long).push_back(r);
+  }
+  const int64_t nshort = (int64_t)split.size();
+  split.insert(split.end(), split_long.begin(), split_long.end());
 
   // -- handle and device arrays ---------------------------------------------
   mpspmv_mat* h = new mpspmv_mat();
@@ -206,6 +213,7 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
   h->ntiles = ntiles;
   h->tlen = tlen;
   h->nsplit = (int64_t)split.size();
+  h->nshort = nshort;
   int st = MPSPMV_OK;
 #define TRY(x)                     \
   do {                             \
@@ -337,6 +345,7 @@ int mpspmv_get_info(mpspmv_h h, mpspmv_info* info) {
   info->chunk = h->K;
   info->flags = h->flags;
   info->device_bytes = h->device_bytes;
+  info->nlong_rows = h->nsplit - h->nshort;
   return MPSPMV_OK;
 }
 

@@ -32,9 +32,13 @@ struct DevMat {
   const int32_t* cols;      // tlen, tiled
   const double* vals;       // Pv planes of tlen, tiled
   const int64_t* chunk_row; // nchunks: the row holding entry c*K
-  const int64_t* split_rows;// rows whose entries span > 1 chunk
-  int64_t nsplit;
+  const int64_t* split_rows;// rows whose entries span > 1 chunk: the nshort rows
+                            // spanning at most kLongSpan chunks, then the rest
+  int64_t nsplit, nshort;
 };
+
+// Rows whose entries span more than this many chunks are combined by a warp.
+constexpr int kLongSpan = 32;
 
 struct mpspmv_mat {
   int device;
@@ -43,7 +47,7 @@ struct mpspmv_mat {
   unsigned flags;
   int64_t nrows, ncols, nnz, max_row_nnz;
   int32_t K;
-  int64_t nchunks, ntiles, tlen, nsplit;
+  int64_t nchunks, ntiles, tlen, nsplit, nshort;
   int64_t* d_indptr = nullptr;
   int32_t* d_cols = nullptr;
   double* d_vals = nullptr;
@@ -62,7 +66,7 @@ struct mpspmv_mat {
     DevMat m;
     m.nrows = nrows; m.ncols = ncols; m.nnz = nnz; m.nchunks = nchunks; m.tlen = tlen; m.K = K;
     m.indptr = d_indptr; m.cols = d_cols; m.vals = d_vals; m.chunk_row = d_chunk_row;
-    m.split_rows = d_split; m.nsplit = nsplit;
+    m.split_rows = d_split; m.nsplit = nsplit; m.nshort = nshort;
     return m;
   }
 };

@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kThreads) spmv_runs_kernel(DevMat m, const dou
 
 // Rows cut by run boundaries: partial of the run where the row starts (slot
 // w = 1), then the partials of the following runs (slot w = 0) in order.
+// One thread per (row, right-hand side) for rows spanning few runs.
 template <int L, bool CPLX>
 __global__ void __launch_bounds__(kThreads) combine_kernel(DevMat m, double* __restrict__ y, int64_t ys,
                                                            int64_t yoff, const double* __restrict__ carry,
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(DevMat m, double* __r
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t s = t / k;
   const int rhs = (int)(t - s * k);
-  if (s >= m.nsplit) return;
+  if (s >= m.nshort) return;
   const int64_t r = __ldg(m.split_rows + s);
   const int64_t c0 = __ldg(m.indptr + r) / m.K;
   const int64_t c1 = (__ldg(m.indptr + r + 1) - 1) / m.K;
@@ -219,6 +220,68 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(DevMat m, double* __r
     }
   }
   store_mp<L, CPLX>(y + rhs, ys, r * yoff, sr, si);
+}
+
+template <int L>
+__device__ __forceinline__ mp<L> shfl_down_mp(const mp<L>& a, int off) {
+  mp<L> r;
+#pragma unroll
+  for (int l = 0; l < L; l++) r.v[l] = __shfl_down_sync(0xffffffffu, a.v[l], off);
+  return r;
+}
+
+// Rows spanning many runs (power-law rows): one warp per (row, right-hand
+// side).  Lane l sums the following-run partials c0+1+l, c0+1+l+32, ... in
+// order, a shuffle tree adds the 32 lane sums, and the starting run's partial
+// goes in front.
+template <int L, bool CPLX>
+__global__ void __launch_bounds__(kThreads) combine_long_kernel(DevMat m, double* __restrict__ y, int64_t ys,
+                                                                int64_t yoff, const double* __restrict__ carry,
+                                                                int kc, int k, const int* __restrict__ gate) {
+  constexpr int P = CPLX ? 2 * L : L;
+  if (gate && *gate != 0) return;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t s = wid / k;
+  const int rhs = (int)(wid - s * k);
+  if (s >= m.nsplit - m.nshort) return;  // whole warp leaves together
+  const int64_t r = __ldg(m.split_rows + m.nshort + s);
+  const int64_t c0 = __ldg(m.indptr + r) / m.K;
+  const int64_t c1 = (__ldg(m.indptr + r + 1) - 1) / m.K;
+  auto ld = [&](int w, int p, int64_t c) { return carry[((int64_t)(w * P + p) * m.nchunks + c) * kc + rhs]; };
+  mp<L> sr = mp_zero<L>(), si = mp_zero<L>();
+  for (int64_t c = c0 + 1 + lane; c <= c1; c += 32) {
+    mp<L> ar, ai;
+#pragma unroll
+    for (int l = 0; l < L; l++) ar.v[l] = ld(0, l, c);
+    sr = mp_add<L>(sr, ar);
+    if (CPLX) {
+#pragma unroll
+      for (int l = 0; l < L; l++) ai.v[l] = ld(0, L + l, c);
+      si = mp_add<L>(si, ai);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    mp<L> o = shfl_down_mp<L>(sr, off);
+    if (lane < off) sr = mp_add<L>(sr, o);
+    if (CPLX) {
+      o = shfl_down_mp<L>(si, off);
+      if (lane < off) si = mp_add<L>(si, o);
+    }
+  }
+  if (lane == 0) {
+    mp<L> fr, fi;
+#pragma unroll
+    for (int l = 0; l < L; l++) fr.v[l] = ld(1, l, c0);
+    fr = mp_add<L>(fr, sr);
+    if (CPLX) {
+#pragma unroll
+      for (int l = 0; l < L; l++) fi.v[l] = ld(1, L + l, c0);
+      fi = mp_add<L>(fi, si);
+    }
+    store_mp<L, CPLX>(y + rhs, ys, r * yoff, fr, fi);
+  }
 }
 
 // y = 0 (single right-hand side), gated
@@ -259,10 +322,16 @@ int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, d
   spmv_runs_kernel<L, CPLX, MIXED><<<(unsigned)blocks, kThreads, 0, s>>>(m, x, xs, xoff, y, ys, yoff, h->d_carry,
                                                                         h->carry_k, kp, k, gate);
   MPS_CUDA(cudaGetLastError());
-  if (h->nsplit > 0) {
-    const int64_t ct = h->nsplit * k;
+  if (h->nshort > 0) {
+    const int64_t ct = h->nshort * k;
     combine_kernel<L, CPLX><<<(unsigned)((ct + kThreads - 1) / kThreads), kThreads, 0, s>>>(m, y, ys, yoff, h->d_carry,
                                                                                          h->carry_k, k, gate);
+    MPS_CUDA(cudaGetLastError());
+  }
+  if (h->nsplit > h->nshort) {
+    const int64_t ct = (h->nsplit - h->nshort) * k * 32;
+    combine_long_kernel<L, CPLX><<<(unsigned)((ct + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        m, y, ys, yoff, h->d_carry, h->carry_k, k, gate);
     MPS_CUDA(cudaGetLastError());
   }
   return MPSPMV_OK;

@@ -172,6 +172,38 @@ int mpspmv_bicgstab(mpspmv_h h, const double* b, double* x, double rtol, double 
                     double* relres, void* stream);
 
 /*
+ * mpspmv_spmv_csr_noalloc -- y = A x for callers that cannot allocate device
+ * memory when they multiply: a process that has given all of its device
+ * memory to its own pool or arena at start-up, or a latency-bound loop that
+ * cannot take the device-wide synchronisation of cudaMalloc / cudaFree.  The
+ * paper has no counterpart; the arithmetic is that of mpspmv_spmv (runs of 16
+ * stored entries summed one per thread, Algorithms 1-2 / QD sloppy forms),
+ * but the matrix comes as plain caller-owned CSR arrays and no handle is made.
+ *
+ *  prec        1..4 (L).   flags  0 or MPSPMV_COMPLEX (P = L or 2L planes).
+ *  nrows, ncols, nnz   shape; nnz = indptr[nrows] (not read from the device).
+ *  indptr      device, nrows + 1 int64 row offsets, non-decreasing from 0.
+ *  indices     device, nnz int32 column indices, each in [0, ncols).
+ *  vals        device, P planes of nnz binary64 (CSR order, structure of limbs).
+ *  x, y        device, P planes of ncols / nrows; y must not overlap x.
+ *
+ * No cudaMalloc, cudaFree or allocating library call is made.  The partial
+ * sums of rows that cross a run boundary go to a fixed 32 MiB array in the
+ * library's device image (every GPU that loads the library holds it until
+ * the process exits), so nnz may be at most 2^22 / (2 P) * 16 (DD: 16,777,216;
+ * QD complex: 4,194,304); larger problems return MPSPMV_EINVAL.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture.  Every call
+ * shares the array and leaves its partial sums there; each call writes every
+ * slot it reads, so nothing needs clearing, but calls that overlap on the GPU
+ * (two streams, or two host threads) race on it and must be ordered by the
+ * caller.  Asynchronous on `stream`.
+ */
+int mpspmv_spmv_csr_noalloc(int prec, unsigned flags, int64_t nrows, int64_t ncols, int64_t nnz,
+                            const int64_t* indptr, const int32_t* indices, const double* vals, const double* x,
+                            double* y, void* stream);
+
+/*
  * mpspmv_probe_fp64 -- measured binary64 instruction throughput of this GPU
  * at the current clocks (the compute denominator of the SpMV roofline; the
  * paper has no counterpart -- its kernels are CPU SIMD code).

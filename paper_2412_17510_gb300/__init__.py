@@ -61,6 +61,7 @@ def _load():
                       ctypes.POINTER(ctypes.c_double), vp],
         "mpspmv_bicgstab": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
                             ctypes.POINTER(ctypes.c_double), vp],
+        "mpspmv_spmv_csr_noalloc": [c_int, ctypes.c_uint, i64, i64, i64, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -167,6 +168,13 @@ def mpspmv_cg(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=
 def mpspmv_bicgstab(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=False):
     """BiCGSTAB in place on x.  Returns (status, iterations, true relative residual)."""
     return _solve(_lib.mpspmv_bicgstab, "mpspmv_bicgstab", h, b, x, rtol, atol, maxit, stream, raise_on_noconv)
+
+
+def mpspmv_spmv_csr_noalloc(prec, flags, nrows, ncols, nnz, indptr, indices, vals, x, y, stream=None):
+    """y = A x from caller-owned device CSR arrays, with no device allocation
+    (scratch is a fixed array inside the library)."""
+    _check(_lib.mpspmv_spmv_csr_noalloc(prec, flags, nrows, ncols, nnz, _ptr(indptr), _ptr(indices), _ptr(vals),
+                                        _ptr(x), _ptr(y), _stream(stream)), "mpspmv_spmv_csr_noalloc")
 
 
 def mpspmv_probe_fp64(op, iters=4096, stream=None):

@@ -172,6 +172,63 @@ int mpspmv_bicgstab(mpspmv_h h, const double* b, double* x, double rtol, double 
                     double* relres, void* stream);
 
 /*
+ * Batched products and solves over many independent matrices of one
+ * precision (real, P mode, nnz > 0 each), each with k_i right-hand sides
+ * (1 <= k_i <= 32).  The paper multiplies one matrix at a time (Sections 3
+ * and 4); the batch runs hundreds of uneven matrices in one persistent launch.
+ */
+typedef struct mpspmv_batch* mpspmv_batch_h;
+
+#define MPSPMV_BATCH_AUTOTUNE 1u /* time run lengths K and lanes per run w per matrix at creation */
+
+/*
+ * mpspmv_batch_create -- group `count` handles with k[i] right-hand sides.
+ * The handles stay owned by the caller and must outlive the batch; with
+ * MPSPMV_BATCH_AUTOTUNE each handle may be re-cut into runs of another length
+ * (K in {8, 16, 32, 64}, chosen by timing; results stay within the SpMV
+ * bound).  Synchronises `stream`.
+ */
+int mpspmv_batch_create(const mpspmv_h* mats, const int* k, int count, unsigned flags, mpspmv_batch_h* out,
+                        void* stream);
+
+/* Release the batch (not its handles). */
+int mpspmv_batch_destroy(mpspmv_batch_h b);
+
+/* Host arrays of count entries: the run length K and lanes per run w chosen
+ * for each matrix (either may be NULL). */
+int mpspmv_batch_get_plan(mpspmv_batch_h b, int* K, int* w);
+
+/*
+ * mpspmv_batch_spmm -- Y_i = A_i X_i for every matrix in one CUDA graph
+ * launch (queue reset, persistent run kernel, row-boundary combine).
+ *  X, Y      host arrays of count device pointers; matrix i's X and Y use the
+ *            mpspmv_spmm layout with k[i] columns and leading dimensions
+ *            ldx[i], ldy[i] (host arrays; NULL means k[i]).
+ * The graph is cached for the last (X, Y, ldx, ldy) set.  Each column of Y_i
+ * equals mpspmv_spmv on the same handle except that rows spanning more than
+ * 32 runs are combined serially.  Asynchronous.
+ */
+int mpspmv_batch_spmm(mpspmv_batch_h b, const double* const* X, const int64_t* ldx, double* const* Y,
+                      const int64_t* ldy, void* stream);
+
+/*
+ * mpspmv_batch_cg -- CG (as mpspmv_cg, Section 4.2) on every (matrix, column)
+ * system at once: sum(k) independent solves, each with its own scalars and
+ * stopping test, iterations captured in a CUDA graph and replayed until no
+ * system is running.
+ *  B, X      host arrays of count device pointers; n_i x k_i row-major planes
+ *            (ldb, ldx NULL or equal to k[i]).  X holds the initial guesses
+ *            and returns the iterates.
+ *  iters, relres, status   host arrays of sum(k) entries (may be NULL):
+ *            iterations, true relative residual, per-system status.
+ * Returns MPSPMV_EBREAKDOWN if any system broke down, else MPSPMV_ENOCONV if
+ * any reached maxit, else MPSPMV_OK.  Synchronises `stream`.
+ */
+int mpspmv_batch_cg(mpspmv_batch_h b, const double* const* B, const int64_t* ldb, double* const* X,
+                    const int64_t* ldx, double rtol, double atol, int maxit, int* iters, double* relres, int* status,
+                    void* stream);
+
+/*
  * mpspmv_spmv_csr_noalloc -- y = A x for callers that cannot allocate device
  * memory when they multiply: a process that has given all of its device
  * memory to its own pool or arena at start-up, or a latency-bound loop that

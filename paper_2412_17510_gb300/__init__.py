@@ -26,6 +26,7 @@ MPSPMV_ETIMEOUT = -7
 
 MPSPMV_D, MPSPMV_DD, MPSPMV_TD, MPSPMV_QD = 1, 2, 3, 4
 MPSPMV_COMPLEX, MPSPMV_MIXED, MPSPMV_SYMMETRIC, MPSPMV_ONE_BASED = 1, 2, 4, 8
+MPSPMV_BATCH_AUTOTUNE = 1
 
 PREC = {"d": 1, "dd": 2, "td": 3, "qd": 4}
 
@@ -62,6 +63,11 @@ def _load():
         "mpspmv_bicgstab": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
                             ctypes.POINTER(ctypes.c_double), vp],
         "mpspmv_spmv_csr_noalloc": [c_int, ctypes.c_uint, i64, i64, i64, vp, vp, vp, vp, vp, vp],
+        "mpspmv_batch_create": [vp, vp, c_int, ctypes.c_uint, ctypes.POINTER(vp), vp],
+        "mpspmv_batch_destroy": [vp],
+        "mpspmv_batch_get_plan": [vp, vp, vp],
+        "mpspmv_batch_spmm": [vp, vp, vp, vp, vp, vp],
+        "mpspmv_batch_cg": [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -175,6 +181,53 @@ def mpspmv_spmv_csr_noalloc(prec, flags, nrows, ncols, nnz, indptr, indices, val
     (scratch is a fixed array inside the library)."""
     _check(_lib.mpspmv_spmv_csr_noalloc(prec, flags, nrows, ncols, nnz, _ptr(indptr), _ptr(indices), _ptr(vals),
                                         _ptr(x), _ptr(y), _stream(stream)), "mpspmv_spmv_csr_noalloc")
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))(*[_ptr(a) for a in items])
+    return arr
+
+
+def mpspmv_batch_create(mats, ks, flags=0, stream=None):
+    """Batch of handles ``mats`` with ``ks[i]`` right-hand sides each."""
+    hs = (ctypes.c_void_p * len(mats))(*[m.value if isinstance(m, ctypes.c_void_p) else m for m in mats])
+    kk = np.ascontiguousarray(ks, dtype=np.int32)
+    b = ctypes.c_void_p()
+    _check(_lib.mpspmv_batch_create(hs, kk.ctypes.data, len(mats), flags, ctypes.byref(b), _stream(stream)),
+           "mpspmv_batch_create")
+    return b
+
+
+def mpspmv_batch_destroy(b):
+    _check(_lib.mpspmv_batch_destroy(b), "mpspmv_batch_destroy")
+
+
+def mpspmv_batch_get_plan(b, count):
+    K = np.zeros(count, dtype=np.int32)
+    w = np.zeros(count, dtype=np.int32)
+    _check(_lib.mpspmv_batch_get_plan(b, K.ctypes.data, w.ctypes.data), "mpspmv_batch_get_plan")
+    return K, w
+
+
+def mpspmv_batch_spmm(b, X, Y, ldx=None, ldy=None, stream=None):
+    """X, Y: lists of device arrays (one per matrix)."""
+    lx = None if ldx is None else np.ascontiguousarray(ldx, dtype=np.int64)
+    ly = None if ldy is None else np.ascontiguousarray(ldy, dtype=np.int64)
+    _check(_lib.mpspmv_batch_spmm(b, _ptr_array(X), None if lx is None else lx.ctypes.data, _ptr_array(Y),
+                                  None if ly is None else ly.ctypes.data, _stream(stream)), "mpspmv_batch_spmm")
+
+
+def mpspmv_batch_cg(b, B, X, nsys, rtol, atol=0.0, maxit=1000, stream=None):
+    """Batched CG in place on X.  Returns (status, iters[nsys], relres[nsys],
+    per-system status[nsys])."""
+    it = np.zeros(nsys, dtype=np.int32)
+    rr = np.zeros(nsys)
+    ss = np.zeros(nsys, dtype=np.int32)
+    st = _lib.mpspmv_batch_cg(b, _ptr_array(B), None, _ptr_array(X), None, rtol, atol, maxit, it.ctypes.data,
+                              rr.ctypes.data, ss.ctypes.data, _stream(stream))
+    if st not in (MPSPMV_OK, MPSPMV_ENOCONV, MPSPMV_EBREAKDOWN):
+        raise MpspmvError(st, "mpspmv_batch_cg")
+    return st, it, rr, ss
 
 
 def mpspmv_probe_fp64(op, iters=4096, stream=None):

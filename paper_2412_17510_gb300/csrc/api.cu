@@ -55,6 +55,33 @@ int32_t pick_chunk(int64_t nnz) {
   return K;
 }
 
+}  // namespace
+
+void mps_plan(const int64_t* indptr, int64_t nrows, int64_t nnz, int32_t K, std::vector<int64_t>& chunk_row,
+              std::vector<int64_t>& split, int64_t& nshort) {
+  const int64_t nchunks = (nnz + K - 1) / K;
+  chunk_row.assign(nchunks, 0);
+  int64_t r = 0;
+  for (int64_t c = 0; c < nchunks; c++) {
+    const int64_t k0 = c * K;
+    while (indptr[r + 1] <= k0) r++;
+    chunk_row[c] = r;
+  }
+  // rows cut by run boundaries: short spans first, then the long ones
+  split.clear();
+  std::vector<int64_t> split_long;
+  for (int64_t i = 0; i < nrows; i++) {
+    if (indptr[i + 1] <= indptr[i]) continue;
+    const int64_t span = (indptr[i + 1] - 1) / K - indptr[i] / K;
+    if (span == 0) continue;
+    (span <= kLongSpan ? split : split_long).push_back(i);
+  }
+  nshort = (int64_t)split.size();
+  split.insert(split.end(), split_long.begin(), split_long.end());
+}
+
+namespace {
+
 struct DeviceScratch {
   std::vector<void*> ptrs;
   ~DeviceScratch() {
@@ -175,25 +202,9 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
   const int64_t nchunks = (nnz + K - 1) / K;
   const int64_t ntiles = (nchunks + 31) / 32;
   const int64_t tlen = ntiles * 32 * (int64_t)K;
-  std::vector<int64_t> chunk_row(nchunks);
-  {
-    int64_t r = 0;
-    for (int64_t c = 0; c < nchunks; c++) {
-      const int64_t k0 = c * K;
-      while (indptr[r + 1] <= k0) r++;
-      chunk_row[c] = r;
-    }
-  }
-  // rows cut by run boundaries: short spans first, then the long ones
-  std::vector<int64_t> split, split_long;
-  for (int64_t r = 0; r < nrows; r++) {
-    if (indptr[r + 1] <= indptr[r]) continue;
-    const int64_t span = (indptr[r + 1] - 1) / K - indptr[r] / K;
-    if (span == 0) continue;
-    (span <= kLongSpan ? split : split_long).push_back(r);
-  }
-  const int64_t nshort = (int64_t)split.size();
-  split.insert(split.end(), split_long.begin(), split_long.end());
+  std::vector<int64_t> chunk_row, split;
+  int64_t nshort = 0;
+  mps_plan(indptr.data(), nrows, nnz, K, chunk_row, split, nshort);
 
   // -- handle and device arrays ---------------------------------------------
   mpspmv_mat* h = new mpspmv_mat();
@@ -214,6 +225,7 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
   h->tlen = tlen;
   h->nsplit = (int64_t)split.size();
   h->nshort = nshort;
+  h->h_indptr = indptr;
   int st = MPSPMV_OK;
 #define TRY(x)                     \
   do {                             \

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/mpspmv.h"
 
 #define MPS_CUDA(call)                              \
@@ -61,6 +63,7 @@ struct mpspmv_mat {
   int64_t kws_len = 0;
   struct KrylovState* d_kstate = nullptr;
   int64_t device_bytes = 0;
+  std::vector<int64_t> h_indptr;  // host copy of the row offsets (re-planning)
 
   DevMat view() const {
     DevMat m;
@@ -82,5 +85,12 @@ int mps_launch_spmv_if_running(const mpspmv_mat* h, const double* x, double* y, 
 int mps_launch_spmm(mpspmv_mat* h, int k, const double* X, int64_t ldx, double* Y, int64_t ldy,
                     cudaStream_t s);
 int mps_ensure_carry(mpspmv_mat* h, int k);
+// Run plan for runs of K entries: chunk_row[c] = row holding entry c*K; split
+// = rows spanning more than one run, the nshort spanning at most kLongSpan
+// runs first.
+void mps_plan(const int64_t* indptr, int64_t nrows, int64_t nnz, int32_t K, std::vector<int64_t>& chunk_row,
+              std::vector<int64_t>& split, int64_t& nshort);
+// Re-cut the stored entries of h into runs of K entries (tiles, plan, carry).
+int mps_retile(mpspmv_mat* h, int32_t K, cudaStream_t s);
 
 static inline cudaStream_t mps_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }

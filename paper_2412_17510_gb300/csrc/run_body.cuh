@@ -1,0 +1,122 @@
+// run_body.cuh -- per-run summation shared by the single-matrix SpMV/SpMM
+// kernels and the batched persistent kernel (arXiv 2412.17510, Section 3;
+// complex by Eq. complex_spmv).
+#pragma once
+#include "internal.h"
+#include "mp_arith.cuh"
+
+namespace mpk {
+
+__device__ __forceinline__ int64_t tile_pos(int64_t c, int j, int K) {
+  return (c >> 5) * (32 * (int64_t)K) + (int64_t)j * 32 + (c & 31);
+}
+
+// ---------------------------------------------------------------------------
+// Per-entry contribution: (sr, si) += a * x[col]  (Eq. complex_spmv order:
+// re += a_re x_re; re += -(a_im x_im); im += a_re x_im; im += a_im x_re).
+// ---------------------------------------------------------------------------
+template <int L, bool CPLX, bool MIXED>
+__device__ __forceinline__ void accumulate(const DevMat& m, int64_t pos, const double* __restrict__ x,
+                                           int64_t xs, int64_t xcol_off, mp<L>& sr, mp<L>& si) {
+  const int64_t col = __ldg(m.cols + pos);
+  mp<L> xr, xi;
+#pragma unroll
+  for (int l = 0; l < L; l++) xr.v[l] = __ldg(x + (int64_t)l * xs + col * xcol_off);
+  if (CPLX) {
+#pragma unroll
+    for (int l = 0; l < L; l++) xi.v[l] = __ldg(x + (int64_t)(L + l) * xs + col * xcol_off);
+  }
+  if (MIXED) {
+    const double ar = __ldg(m.vals + pos);
+    sr = mp_add<L>(sr, mp_mul_d<L>(xr, ar));
+    if (CPLX) {
+      const double ai = __ldg(m.vals + m.tlen + pos);
+      sr = mp_add<L>(sr, mp_neg<L>(mp_mul_d<L>(xi, ai)));
+      si = mp_add<L>(si, mp_mul_d<L>(xi, ar));
+      si = mp_add<L>(si, mp_mul_d<L>(xr, ai));
+    }
+  } else {
+    mp<L> ar;
+#pragma unroll
+    for (int l = 0; l < L; l++) ar.v[l] = __ldg(m.vals + (int64_t)l * m.tlen + pos);
+    sr = mp_add<L>(sr, mp_mul<L>(ar, xr));
+    if (CPLX) {
+      mp<L> ai;
+#pragma unroll
+      for (int l = 0; l < L; l++) ai.v[l] = __ldg(m.vals + (int64_t)(L + l) * m.tlen + pos);
+      sr = mp_add<L>(sr, mp_neg<L>(mp_mul<L>(ai, xi)));
+      si = mp_add<L>(si, mp_mul<L>(ar, xi));
+      si = mp_add<L>(si, mp_mul<L>(ai, xr));
+    }
+  }
+}
+
+template <int L, bool CPLX>
+__device__ __forceinline__ void store_mp(double* __restrict__ out, int64_t ps, int64_t idx, const mp<L>& sr,
+                                         const mp<L>& si) {
+#pragma unroll
+  for (int l = 0; l < L; l++) out[(int64_t)l * ps + idx] = sr.v[l];
+  if (CPLX) {
+#pragma unroll
+    for (int l = 0; l < L; l++) out[(int64_t)(L + l) * ps + idx] = si.v[l];
+  }
+}
+
+// One thread sums run c (entries c*K .. c*K+K-1, left to right) for the
+// right-hand side rhs: a row that ends inside the run is written to y, the
+// partial sum of a row cut by a run boundary goes to the carry buffer (slot
+// w = 0 when the row started before the run, w = 1 when it continues past it).
+// Carry layout: carry[((w*P + p)*nchunks + c)*kc + rhs].
+template <int L, bool CPLX, bool MIXED>
+__device__ __forceinline__ void process_run(const DevMat& m, int64_t c, int rhs, const double* __restrict__ x,
+                                            int64_t xs, int64_t xoff, double* __restrict__ y, int64_t ys,
+                                            int64_t yoff, double* __restrict__ carry, int kc) {
+  constexpr int P = CPLX ? 2 * L : L;
+  const double* xr = x + rhs;
+  double* yr = y + rhs;
+  const int64_t k0 = c * m.K;
+  const int64_t k1 = min(k0 + (int64_t)m.K, m.nnz);
+  int64_t row = __ldg(m.chunk_row + c);
+  const int64_t first_row = row;
+  const bool first_partial = __ldg(m.indptr + row) < k0;
+  int64_t rend = __ldg(m.indptr + row + 1);
+  const mp<L> z = mp_zero<L>();
+  if (c == 0) {  // rows before the first stored entry are empty
+    for (int64_t r = 0; r < row; r++) store_mp<L, CPLX>(yr, ys, r * yoff, z, z);
+  }
+  mp<L> sr = z, si = z;
+  bool have = false;
+  const int n = (int)(k1 - k0);
+  const int64_t chunk_base = tile_pos(c, 0, m.K);
+  for (int j = 0; j < n; j++) {
+    accumulate<L, CPLX, MIXED>(m, chunk_base + (int64_t)j * 32, xr, xs, xoff, sr, si);
+    have = true;
+    const int64_t kk = k0 + j + 1;
+    if (kk == rend) {
+      if (row == first_row && first_partial) {
+#pragma unroll
+        for (int p = 0; p < P; p++)
+          carry[((int64_t)(0 * P + p) * m.nchunks + c) * kc + rhs] = p < L ? sr.v[p % L] : si.v[p % L];
+      } else {
+        store_mp<L, CPLX>(yr, ys, row * yoff, sr, si);
+      }
+      sr = z;
+      si = z;
+      have = false;
+      row++;
+      while (row < m.nrows && __ldg(m.indptr + row + 1) == kk) {  // empty rows at this position
+        store_mp<L, CPLX>(yr, ys, row * yoff, z, z);
+        row++;
+      }
+      rend = row < m.nrows ? __ldg(m.indptr + row + 1) : INT64_MAX;
+    }
+  }
+  if (have) {
+    const int w = (row == first_row && first_partial) ? 0 : 1;
+#pragma unroll
+    for (int p = 0; p < P; p++)
+      carry[((int64_t)(w * P + p) * m.nchunks + c) * kc + rhs] = p < L ? sr.v[p % L] : si.v[p % L];
+  }
+}
+
+}  // namespace mpk

@@ -19,16 +19,13 @@
 
 #include "internal.h"
 #include "mp_arith.cuh"
+#include "run_body.cuh"
 
 using namespace mpk;
 
 namespace {
 
 constexpr int kThreads = 128;
-
-__device__ __forceinline__ int64_t tile_pos(int64_t c, int j, int K) {
-  return (c >> 5) * (32 * (int64_t)K) + (int64_t)j * 32 + (c & 31);
-}
 
 // ---------------------------------------------------------------------------
 // Build: sorted triplets (duplicates adjacent) -> tiled column / value arrays.
@@ -69,57 +66,6 @@ __global__ void build_tiles_kernel(DevMat m, int32_t* __restrict__ cols_out, dou
 }
 
 // ---------------------------------------------------------------------------
-// Per-entry contribution: (sr, si) += a * x[col]  (Eq. complex_spmv order:
-// re += a_re x_re; re += -(a_im x_im); im += a_re x_im; im += a_im x_re).
-// ---------------------------------------------------------------------------
-template <int L, bool CPLX, bool MIXED>
-__device__ __forceinline__ void accumulate(const DevMat& m, int64_t pos, const double* __restrict__ x,
-                                           int64_t xs, int64_t xcol_off, mp<L>& sr, mp<L>& si) {
-  const int64_t col = __ldg(m.cols + pos);
-  mp<L> xr, xi;
-#pragma unroll
-  for (int l = 0; l < L; l++) xr.v[l] = __ldg(x + (int64_t)l * xs + col * xcol_off);
-  if (CPLX) {
-#pragma unroll
-    for (int l = 0; l < L; l++) xi.v[l] = __ldg(x + (int64_t)(L + l) * xs + col * xcol_off);
-  }
-  if (MIXED) {
-    const double ar = __ldg(m.vals + pos);
-    sr = mp_add<L>(sr, mp_mul_d<L>(xr, ar));
-    if (CPLX) {
-      const double ai = __ldg(m.vals + m.tlen + pos);
-      sr = mp_add<L>(sr, mp_neg<L>(mp_mul_d<L>(xi, ai)));
-      si = mp_add<L>(si, mp_mul_d<L>(xi, ar));
-      si = mp_add<L>(si, mp_mul_d<L>(xr, ai));
-    }
-  } else {
-    mp<L> ar;
-#pragma unroll
-    for (int l = 0; l < L; l++) ar.v[l] = __ldg(m.vals + (int64_t)l * m.tlen + pos);
-    sr = mp_add<L>(sr, mp_mul<L>(ar, xr));
-    if (CPLX) {
-      mp<L> ai;
-#pragma unroll
-      for (int l = 0; l < L; l++) ai.v[l] = __ldg(m.vals + (int64_t)(L + l) * m.tlen + pos);
-      sr = mp_add<L>(sr, mp_neg<L>(mp_mul<L>(ai, xi)));
-      si = mp_add<L>(si, mp_mul<L>(ar, xi));
-      si = mp_add<L>(si, mp_mul<L>(ai, xr));
-    }
-  }
-}
-
-template <int L, bool CPLX>
-__device__ __forceinline__ void store_mp(double* __restrict__ out, int64_t ps, int64_t idx, const mp<L>& sr,
-                                         const mp<L>& si) {
-#pragma unroll
-  for (int l = 0; l < L; l++) out[(int64_t)l * ps + idx] = sr.v[l];
-  if (CPLX) {
-#pragma unroll
-    for (int l = 0; l < L; l++) out[(int64_t)(L + l) * ps + idx] = si.v[l];
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Run kernel.  Vectors: x plane stride xs, entry j at x[j*xoff] within a plane
 // (xoff = ldx for SpMM, 1 for SpMV); y likewise.  rhs selects the column of a
 // multi-right-hand-side product (0 for SpMV); `kp` threads share a run.
@@ -131,57 +77,12 @@ __global__ void __launch_bounds__(kThreads) spmv_runs_kernel(DevMat m, const dou
                                                              int64_t xoff, double* __restrict__ y, int64_t ys,
                                                              int64_t yoff, double* __restrict__ carry, int kc,
                                                              int kp, int k, const int* __restrict__ gate) {
-  constexpr int P = CPLX ? 2 * L : L;
   if (gate && *gate != 0) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t c = t / kp;
   const int rhs = (int)(t - c * kp);
   if (c >= m.nchunks || rhs >= k) return;
-  const double* xr = x + rhs;
-  double* yr = y + rhs;
-  const int64_t k0 = c * m.K;
-  const int64_t k1 = min(k0 + (int64_t)m.K, m.nnz);
-  int64_t row = __ldg(m.chunk_row + c);
-  const int64_t first_row = row;
-  const bool first_partial = __ldg(m.indptr + row) < k0;
-  int64_t rend = __ldg(m.indptr + row + 1);
-  const mp<L> z = mp_zero<L>();
-  if (c == 0) {  // rows before the first stored entry are empty
-    for (int64_t r = 0; r < row; r++) store_mp<L, CPLX>(yr, ys, r * yoff, z, z);
-  }
-  mp<L> sr = z, si = z;
-  bool have = false;
-  const int n = (int)(k1 - k0);
-  const int64_t chunk_base = tile_pos(c, 0, m.K);
-  for (int j = 0; j < n; j++) {
-    accumulate<L, CPLX, MIXED>(m, chunk_base + (int64_t)j * 32, xr, xs, xoff, sr, si);
-    have = true;
-    const int64_t kk = k0 + j + 1;
-    if (kk == rend) {
-      if (row == first_row && first_partial) {
-#pragma unroll
-        for (int p = 0; p < P; p++)
-          carry[((int64_t)(0 * P + p) * m.nchunks + c) * kc + rhs] = p < L ? sr.v[p % L] : si.v[p % L];
-      } else {
-        store_mp<L, CPLX>(yr, ys, row * yoff, sr, si);
-      }
-      sr = z;
-      si = z;
-      have = false;
-      row++;
-      while (row < m.nrows && __ldg(m.indptr + row + 1) == kk) {  // empty rows at this position
-        store_mp<L, CPLX>(yr, ys, row * yoff, z, z);
-        row++;
-      }
-      rend = row < m.nrows ? __ldg(m.indptr + row + 1) : INT64_MAX;
-    }
-  }
-  if (have) {
-    const int w = (row == first_row && first_partial) ? 0 : 1;
-#pragma unroll
-    for (int p = 0; p < P; p++)
-      carry[((int64_t)(w * P + p) * m.nchunks + c) * kc + rhs] = p < L ? sr.v[p % L] : si.v[p % L];
-  }
+  process_run<L, CPLX, MIXED>(m, c, rhs, x, xs, xoff, y, ys, yoff, carry, kc);
 }
 
 // Rows cut by run boundaries: partial of the run where the row starts (slot
@@ -407,4 +308,85 @@ int mps_launch_spmm(mpspmv_mat* h, int k, const double* X, int64_t ldx, double* 
   int st = mps_ensure_carry(h, k);
   if (st != MPSPMV_OK) return st;
   MPS_DISPATCH(launch_all, h, h, X, h->ncols * ldx, ldx, Y, h->nrows * ldy, ldy, k, nullptr, s);
+}
+
+// ---------------------------------------------------------------------------
+// Re-cut the stored entries into runs of a different length (used by the
+// batched autotuner): entry u moves from its tiled position for the old run
+// length to its tiled position for the new one.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void retile_kernel(int64_t nnz, int32_t Kold, int32_t Knew, const int32_t* __restrict__ cols_old,
+                              const double* __restrict__ vals_old, int64_t tlen_old, int32_t* __restrict__ cols_new,
+                              double* __restrict__ vals_new, int64_t tlen_new, int Pv) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= nnz) return;
+  const int64_t co = u / Kold, cn = u / Knew;
+  const int64_t po = tile_pos(co, (int)(u - co * Kold), Kold);
+  const int64_t pn = tile_pos(cn, (int)(u - cn * Knew), Knew);
+  cols_new[pn] = cols_old[po];
+  for (int p = 0; p < Pv; p++) vals_new[(int64_t)p * tlen_new + pn] = vals_old[(int64_t)p * tlen_old + po];
+}
+}  // namespace
+
+int mps_retile(mpspmv_mat* h, int32_t K, cudaStream_t s) {
+  if (K == h->K) return MPSPMV_OK;
+  if (K < 1 || K > 1024) return MPSPMV_EINVAL;
+  const int64_t nchunks = (h->nnz + K - 1) / K;
+  const int64_t ntiles = (nchunks + 31) / 32;
+  const int64_t tlen = ntiles * 32 * (int64_t)K;
+  std::vector<int64_t> chunk_row, split;
+  int64_t nshort = 0;
+  mps_plan(h->h_indptr.data(), h->nrows, h->nnz, K, chunk_row, split, nshort);
+  int32_t* cols = nullptr;
+  double* vals = nullptr;
+  int64_t* crow = nullptr;
+  int64_t* spl = nullptr;
+  double* carry = nullptr;
+  const int kc = std::max(h->carry_k, 1);
+  auto fail = [&](int st) {
+    cudaFree(cols); cudaFree(vals); cudaFree(crow); cudaFree(spl); cudaFree(carry);
+    cudaGetLastError();
+    return st;
+  };
+  if (cudaMalloc(&cols, sizeof(int32_t) * std::max<int64_t>(tlen, 1)) != cudaSuccess ||
+      cudaMalloc(&vals, sizeof(double) * h->Pv * std::max<int64_t>(tlen, 1)) != cudaSuccess ||
+      cudaMalloc(&crow, sizeof(int64_t) * std::max<int64_t>(nchunks, 1)) != cudaSuccess ||
+      cudaMalloc(&spl, sizeof(int64_t) * std::max<size_t>(split.size(), 1)) != cudaSuccess ||
+      cudaMalloc(&carry, sizeof(double) * 2 * h->P * std::max<int64_t>(nchunks, 1) * kc) != cudaSuccess)
+    return fail(MPSPMV_ENOMEM);
+  if (cudaMemsetAsync(cols, 0, sizeof(int32_t) * tlen, s) != cudaSuccess ||
+      cudaMemsetAsync(vals, 0, sizeof(double) * h->Pv * tlen, s) != cudaSuccess ||
+      (nchunks && cudaMemcpyAsync(crow, chunk_row.data(), sizeof(int64_t) * nchunks, cudaMemcpyHostToDevice, s) !=
+                      cudaSuccess) ||
+      (!split.empty() && cudaMemcpyAsync(spl, split.data(), sizeof(int64_t) * split.size(), cudaMemcpyHostToDevice,
+                                         s) != cudaSuccess))
+    return fail(MPSPMV_ECUDA);
+  if (h->nnz > 0) {
+    retile_kernel<<<(unsigned)((h->nnz + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        h->nnz, h->K, K, h->d_cols, h->d_vals, h->tlen, cols, vals, tlen, h->Pv);
+    if (cudaGetLastError() != cudaSuccess) return fail(MPSPMV_ECUDA);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(MPSPMV_ECUDA);
+  h->device_bytes += (int64_t)(sizeof(int32_t) + sizeof(double) * h->Pv) * (tlen - h->tlen) +
+                     (int64_t)sizeof(int64_t) * ((nchunks - h->nchunks) + ((int64_t)split.size() - h->nsplit)) +
+                     (int64_t)sizeof(double) * 2 * h->P * kc * (nchunks - h->nchunks);
+  cudaFree(h->d_cols);
+  cudaFree(h->d_vals);
+  cudaFree(h->d_chunk_row);
+  cudaFree(h->d_split);
+  cudaFree(h->d_carry);
+  h->d_cols = cols;
+  h->d_vals = vals;
+  h->d_chunk_row = crow;
+  h->d_split = spl;
+  h->d_carry = carry;
+  h->carry_k = kc;
+  h->K = K;
+  h->nchunks = nchunks;
+  h->ntiles = ntiles;
+  h->tlen = tlen;
+  h->nsplit = (int64_t)split.size();
+  h->nshort = nshort;
+  return MPSPMV_OK;
 }

@@ -295,3 +295,34 @@ def random_sparse(nrows, ncols, row_len_max, seed=0, cplx=False, L=1, full_limb=
         V = 2 if cplx else 1
         v = rng.standard_normal((V, nnz))
     return COO(nrows, ncols, r, c, v, "rand_%dx%d" % (nrows, ncols))
+
+
+def selector_system(n, log10_cond, seed=0, nnz_range=(8, 24)):
+    """SPD system A = D (L L^T + I) D for the precision selector: L unit lower
+    triangular with U{nnz_range} off-diagonal entries per row (positions
+    uniform in [0, i), values N(0,1)); D = diag(10^t_i) with t_i graded
+    linearly over the rows so that cond(A) is about 10^log10_cond (cond(L L^T
+    + I) is of order 1e2 for these sizes, cond(D)^2 supplies the rest).
+    Returns (COO, b) with b ~ U[-1, 1] in binary64."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    lo, hi = nnz_range
+    for i in range(1, n):
+        m = min(i, int(rng.integers(lo, hi + 1)))
+        c = rng.choice(i, m, replace=False)
+        rows.append(np.full(m, i))
+        cols.append(c)
+        vals.append(rng.standard_normal(m))
+    rows.append(np.arange(n))
+    cols.append(np.arange(n))
+    vals.append(np.ones(n))
+    Lm = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    M = (Lm @ Lm.T + sp.identity(n)).tocsr()
+    tau = max(0.0, (log10_cond - 2.0) / 2.0)
+    d = 10.0 ** (tau * np.arange(n) / max(n - 1, 1))
+    A = (sp.diags(d) @ M @ sp.diags(d)).tocoo()
+    order = np.lexsort((A.col, A.row))
+    coo = COO(n, n, A.row[order], A.col[order], A.data[order][None, :], "selector_n%d_c%g" % (n, log10_cond))
+    b = rng.uniform(-1.0, 1.0, n)
+    return coo, b

@@ -231,6 +231,150 @@ def config_block(mats):
         "precisions": [PNAME[L] for L in PRECS]}
 
 
+
+# ---------------------------------------------------------------------------
+# --suite: the other workloads (complex SpMV + BiCGSTAB, batched SpMM + CG,
+# learned selector).  Reported under "suite" in the JSON line.
+# ---------------------------------------------------------------------------
+def _time_events(fn, reps, stream):
+    import torch
+    evs = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+
+def suite_complex(mps, fp64_fma, hbm, stream, small):
+    """Complex-symmetric band, half-bandwidth 48, 30% fill (n = 500,000):
+    complex DD / QD SpMV, and BiCGSTAB on A + (50+10i) I to 1e-28."""
+    import torch
+    n = 50000 if small else 500000
+    coo = workloads.complex_sym_banded(n, 48, 0.3, seed=0)
+    out = {"workload": "complex-symmetric band n=%d hbw=48 fill 0.3 (nnz=%d complex)" % (n, coo.nnz)}
+    for L in (2, 4):
+        h = mps.mpspmv_create_csr(n, n, coo.row, coo.col, coo.val, L, mps.MPSPMV_COMPLEX, val_limbs=1)
+        x = torch.from_numpy(workloads.full_limb_vector(n, L, seed=0, cplx=True)).cuda()
+        y = torch.empty_like(x)
+        for _ in range(3):
+            mps.mpspmv_spmv(h, x, y, stream)
+        ms = _time_events(lambda: mps.mpspmv_spmv(h, x, y, stream), 10, stream)
+        ops = coo.nnz * 4 * OPS_PER_ENTRY[L]
+        byts = coo.nnz * (4 + 16 * L) + n * (8 + 16 * L) + n * 16 * L
+        troof = max(ops / fp64_fma, byts / (hbm * 1e9))
+        out["spmv_%s" % PNAME[L]] = {"ms": ms, "gnnz_s": coo.nnz / ms / 1e6, "roofline_frac": troof / (ms * 1e-3)}
+        mps.mpspmv_destroy(h)
+    shifted = workloads.complex_sym_banded(n, 48, 0.3, seed=0, shift=50 + 10j)
+    for L in (2, 4):
+        h = mps.mpspmv_create_csr(n, n, shifted.row, shifted.col, shifted.val, L, mps.MPSPMV_COMPLEX, val_limbs=1)
+        xt = torch.from_numpy(workloads.full_limb_vector(n, L, seed=1, cplx=True)).cuda()
+        b = torch.empty_like(xt)
+        mps.mpspmv_spmv(h, xt, b, stream)
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it, rr = mps.mpspmv_bicgstab(h, b, x, 1e-28, 0.0, 5000, stream)
+        torch.cuda.synchronize()
+        out["bicgstab_%s" % PNAME[L]] = {"status": st, "iters": it, "relres": rr, "s": time.perf_counter() - t0}
+        mps.mpspmv_destroy(h)
+    return out
+
+
+def suite_batched(mps, stream, small):
+    """512 SPD 7-point diffusion matrices (kappa log-uniform in [1e-3, 1e3]),
+    n log-uniform in [1e3, 2e5], k ~ U{1..32}: one graph launch of the
+    batched SpMM in DD and QD (autotuned); batched CG to 1e-25 on a reduced
+    set (32 matrices, n in [1e3, 1e4], k ~ U{1..8}) to keep the run short."""
+    import torch
+    count = 64 if small else 512
+    specs = workloads.batch_specs(count, n_range=(1000, 200000), k_range=(1, 32), seed=0)
+    coos = [workloads.diffusion_7pt(nx, ny, nz, seed=sd) for nx, ny, nz, k, sd in specs]
+    ks = [k for *_, k, sd in specs]
+    out = {"workload": "%d diffusion matrices, sum nnz %d, sum k*nnz %d" % (
+        count, sum(c.nnz for c in coos), sum(c.nnz * k for c, k in zip(coos, ks)))}
+    for L in (2, 4):
+        hs = [mps.mpspmv_create_csr(c.nrows, c.ncols, c.row, c.col, c.val, L, 0, val_limbs=1) for c in coos]
+        t0 = time.perf_counter()
+        b = mps.mpspmv_batch_create(hs, ks, mps.MPSPMV_BATCH_AUTOTUNE, stream)
+        tune_s = time.perf_counter() - t0
+        Xs = [torch.from_numpy(np.ascontiguousarray(np.broadcast_to(
+            workloads.full_limb_vector(c.ncols, L, seed=i)[:, :, None], (L, c.ncols, k)))).cuda()
+            for i, (c, k) in enumerate(zip(coos, ks))]
+        Ys = [torch.empty((L, c.nrows, k), dtype=torch.float64, device="cuda") for c, k in zip(coos, ks)]
+        for _ in range(3):
+            mps.mpspmv_batch_spmm(b, Xs, Ys, stream=stream)
+        ms = _time_events(lambda: mps.mpspmv_batch_spmm(b, Xs, Ys, stream=stream), 10, stream)
+        work = sum(c.nnz * k for c, k in zip(coos, ks))
+        K, w = mps.mpspmv_batch_get_plan(b, count)
+        out["spmm_%s" % PNAME[L]] = {"ms_per_launch": ms, "gnnz_rhs_s": work / ms / 1e6, "autotune_s": tune_s,
+                                     "K_hist": {int(v): int((K == v).sum()) for v in np.unique(K)},
+                                     "w_hist": {int(v): int((w == v).sum()) for v in np.unique(w)}}
+        mps.mpspmv_batch_destroy(b)
+        for h in hs:
+            mps.mpspmv_destroy(h)
+        del Xs, Ys
+    # batched CG on the reduced set
+    cspecs = workloads.batch_specs(8 if small else 32, n_range=(1000, 10000), k_range=(1, 8), seed=1)
+    ccoos = [workloads.diffusion_7pt(nx, ny, nz, seed=sd) for nx, ny, nz, k, sd in cspecs]
+    cks = [k for *_, k, sd in cspecs]
+    for L in (2, 4):
+        hs = [mps.mpspmv_create_csr(c.nrows, c.ncols, c.row, c.col, c.val, L, 0, val_limbs=1) for c in ccoos]
+        b = mps.mpspmv_batch_create(hs, cks, 0, stream)
+        Bs = [torch.from_numpy(np.ascontiguousarray(np.stack(
+            [workloads.full_limb_vector(c.ncols, L, seed=100 + i * 40 + j) for j in range(k)], axis=-1))).cuda()
+            for i, (c, k) in enumerate(zip(ccoos, cks))]
+        Xs = [torch.zeros_like(B) for B in Bs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it, rr, ss = mps.mpspmv_batch_cg(b, Bs, Xs, sum(cks), 1e-25, 0.0, 100000, stream)
+        torch.cuda.synchronize()
+        out["cg_%s" % PNAME[L]] = {"systems": int(sum(cks)), "s": time.perf_counter() - t0, "status": st,
+                                   "converged": int((ss == 0).sum()), "iters_max": int(it.max()),
+                                   "iters_mean": float(it.mean()), "relres_max": float(rr.max())}
+        mps.mpspmv_batch_destroy(b)
+        for h in hs:
+            mps.mpspmv_destroy(h)
+    return out
+
+
+def suite_selector(mps, small):
+    """Learned precision selector (scaled: see the design doc): SPD systems
+    A = D (L L^T + I) D, n log-uniform in [40, 160], cond 10^U[8, 40],
+    labelled by the cheapest of binary64 / DD / TD / QD whose CG reaches
+    1e-30 within 30 n iterations; train on the first ones, evaluate on the
+    held-out rest against the plain ladder."""
+    from paper_2412_17510_gb300 import selector as sel
+    ntrain, ntest = (60, 20) if small else (300, 60)
+    rng = np.random.default_rng(0)
+    systems = []
+    for i in range(ntrain + ntest):
+        n = int(round(np.exp(rng.uniform(np.log(40), np.log(160)))))
+        coo, b = workloads.selector_system(n, float(rng.uniform(8, 40)), seed=1000 + i)
+        systems.append(sel.System(coo, b))
+    t0 = time.perf_counter()
+    X = sel.features(systems)
+    y = sel.labels(systems, 1e-30, maxit_factor=30)
+    label_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    params, losses, _ = sel.train(X[:ntrain], y[:ntrain], epochs=300, batch=32, lr=0.05)
+    train_s = time.perf_counter() - t0
+    pred = sel.predict(params, X[ntrain:])
+    ev = sel.evaluate(systems[ntrain:], params, 1e-30, maxit_factor=30)
+    for s in systems:
+        s.free()
+    return {"systems": ntrain + ntest, "train": ntrain, "test": ntest,
+            "label_hist": {int(c): int((y == c).sum()) for c in range(5)},
+            "label_s": label_s, "train_s": train_s, "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "test_accuracy": float((pred == y[ntrain:]).mean()),
+            "escalation_rate": ev["escalated"] / ev["n"],
+            "plain_ladder_s": ev["plain_s"], "selector_ladder_s": ev["auto_s"],
+            "batched_selector_s": ev["batched_auto_s"],
+            "solved": {"plain": ev["plain_ok"], "selector": ev["auto_ok"], "batched_selector": ev["batched_auto_ok"]}}
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -243,6 +387,11 @@ def main():
     ap.add_argument("--small", action="store_true", help="reduced matrices (development)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg")
     ap.add_argument("--only", default=None, help="run one variant, e.g. powerlaw_1e5/QD (profiling)")
+    ap.add_argument("--arith", default="paper", choices=["paper", "exact"],
+                    help="paper: the paper's DD/TD/QD operation sequences; exact: error-free products on the "
+                         "binary64 pipe with exact integer accumulation (MPSPMV_EXACT_ACC)")
+    ap.add_argument("--suite", action="store_true",
+                    help="also measure the complex, batched and selector workloads (adds minutes)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -275,7 +424,8 @@ def main():
         for L in PRECS:
             if args.only and args.only != "%s/%s" % (mname, PNAME[L]):
                 continue
-            h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, 0, val_limbs=1)
+            fl = mps.MPSPMV_EXACT_ACC if args.arith == "exact" else 0
+            h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, fl, val_limbs=1)
             info = mps.mpspmv_get_info(h)
             x = torch.from_numpy(xs_host[mname][L]).cuda()
             y = torch.empty((L, coo.nrows), dtype=torch.float64, device="cuda")
@@ -403,6 +553,12 @@ def main():
 
     for w in variants:
         mps.mpspmv_destroy(w["h"])
+    suite = None
+    if args.suite and rank == 0:
+        del flush
+        suite = {"complex": suite_complex(mps, fp64_fma, hbm, stream, args.small),
+                 "batched": suite_batched(mps, stream, args.small),
+                 "selector": suite_selector(mps, args.small)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -414,6 +570,8 @@ def main():
             "fp64_peak_tinstr_s": {"dfma": fp64_fma / 1e12, "dadd": fp64_add / 1e12},
             "breakdown": breakdown,
         }
+        if suite is not None:
+            line["suite"] = suite
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -55,6 +55,11 @@ typedef enum { MPSPMV_D = 1, MPSPMV_DD = 2, MPSPMV_TD = 3, MPSPMV_QD = 4 } mpspm
 #define MPSPMV_SYMMETRIC 4u /* triplets hold one triangle (Matrix Market "symmetric"):
                                every off-diagonal (i,j,v) also stands for (j,i,v) */
 #define MPSPMV_ONE_BASED 8u /* row/col indices start at 1 (Matrix Market) */
+#define MPSPMV_EXACT_ACC 16u /* GB300 arithmetic variant: per stored entry only the error-free products
+                                (TwoProd by FMA) run on the binary64 pipe and the row sum is accumulated
+                                exactly in fixed point on the integer pipe, then cut to L components.
+                                Same bound 8 m u (|A||x|)_i (usually far smaller error); results are not
+                                bit-identical to the paper-order arithmetic. */
 
 typedef struct mpspmv_mat* mpspmv_h;
 
@@ -227,6 +232,78 @@ int mpspmv_batch_spmm(mpspmv_batch_h b, const double* const* X, const int64_t* l
 int mpspmv_batch_cg(mpspmv_batch_h b, const double* const* B, const int64_t* ldb, double* const* X,
                     const int64_t* ldx, double rtol, double atol, int maxit, int* iters, double* relres, int* status,
                     void* stream);
+
+/*
+ * Precision ladder (binary64 -> DD -> TD -> QD) and the learned selector.
+ * The paper observes that Krylov iteration counts settle as the precision
+ * rises (Section 4.2) and motivates multiple precision by round-off
+ * (Section 1); these entry points choose the precision per system.
+ *
+ * `hs` is a host array of 4 handles of the same real, square, P-mode matrix
+ * at L = 1, 2, 3, 4 (hs[L-1]; NULL skips that level).  b is one binary64
+ * plane of n (device); x is 4 planes of n (device, QD: a level-L iterate uses
+ * the first L planes, the others stay zero, so moving up a level is exact).
+ */
+
+/*
+ * mpspmv_ladder_solve -- x = 0, then CG (mpspmv_cg) at L = start_L, ... 4:
+ * after each level the residual b - A x is recomputed in that level's
+ * precision; when it meets rtol ||b|| + atol the solve stops, otherwise CG
+ * restarts at the next level from the current x.  maxit applies per level.
+ *  final_L  host: last level run.  iters: host array of 4, iterations per
+ *  level.  relres: host, the last recomputed relative residual.
+ * Returns MPSPMV_OK on success, MPSPMV_ENOCONV if no level met the target.
+ * Synchronises `stream`.
+ */
+int mpspmv_ladder_solve(const mpspmv_h* hs, int start_L, const double* b, double* x, double rtol, double atol,
+                        int maxit, int* final_L, int* iters, double* relres, void* stream);
+
+/*
+ * mpspmv_cg_history -- ||r_j|| / ||b||, j = 1..k (k <= 16), of the first k
+ * CG steps from x = 0 on handle h (recurrence residual, h's precision); b has
+ * h's planes.  hist: host array of k.  Synchronises `stream`.
+ */
+int mpspmv_cg_history(mpspmv_h h, const double* b, int k, double* hist, void* stream);
+
+/*
+ * mpspmv_features -- the selector's 32 features of handle h (host floats):
+ * row-length statistics, diagonal dominance, log norms, Gershgorin bounds,
+ * and (when cg_hist, 8 host doubles from mpspmv_cg_history, is given) the
+ * binary64 CG residual history and its slope.  Synchronises `stream`.
+ */
+int mpspmv_features(mpspmv_h h, const double* cg_hist, float* feat, void* stream);
+
+/*
+ * Selector network: float32 MLP 32 -> 128 -> 128 -> C (ReLU hidden layers,
+ * softmax cross-entropy), parameters in one device buffer of
+ * mpspmv_mlp_param_count(C) floats: W1 (32x128), b1, W2 (128x128), b2,
+ * W3 (128xC), b3, row-major, activations h = x W + b.  X: device, B x 32
+ * row-major; y: device int labels in [0, C).
+ */
+int64_t mpspmv_mlp_param_count(int C);
+/* logits: device, B x C. Synchronises `stream`. */
+int mpspmv_mlp_forward(const float* params, int C, const float* X, int B, float* logits, void* stream);
+/* grads: device, same layout as params; loss: host (mean cross-entropy). */
+int mpspmv_mlp_grad(const float* params, int C, const float* X, const int* y, int B, float* grads, float* loss,
+                    void* stream);
+/* `epochs` passes of plain SGD (step lr) over n samples in mini-batches of
+ * `batch` (in data order; a final partial batch is skipped); params updated
+ * in place; loss_per_epoch: host array of epochs (may be NULL). */
+int mpspmv_mlp_train(float* params, int C, const float* X, const int* y, int n, int batch, int epochs, float lr,
+                     float* loss_per_epoch, void* stream);
+
+/*
+ * mpspmv_select_precision -- features of (hs[0], b) (binary64 CG history
+ * included) -> network -> *prec in 1..4 (classes binary64, DD, TD, QD and
+ * "none", which maps to QD).  feat_out: host 32 floats, may be NULL.
+ */
+int mpspmv_select_precision(const mpspmv_h* hs, const float* params, int C, const double* b, int* prec,
+                            float* feat_out, void* stream);
+
+/* mpspmv_solve_auto -- mpspmv_select_precision, then mpspmv_ladder_solve from
+ * the chosen level (the ladder is the fallback when the choice falls short). */
+int mpspmv_solve_auto(const mpspmv_h* hs, const float* params, int C, const double* b, double* x, double rtol,
+                      double atol, int maxit, int* chosen_L, int* final_L, int* iters, double* relres, void* stream);
 
 /*
  * mpspmv_spmv_csr_noalloc -- y = A x for callers that cannot allocate device

@@ -27,6 +27,7 @@ MPSPMV_ETIMEOUT = -7
 MPSPMV_D, MPSPMV_DD, MPSPMV_TD, MPSPMV_QD = 1, 2, 3, 4
 MPSPMV_COMPLEX, MPSPMV_MIXED, MPSPMV_SYMMETRIC, MPSPMV_ONE_BASED = 1, 2, 4, 8
 MPSPMV_BATCH_AUTOTUNE = 1
+MPSPMV_EXACT_ACC = 16
 
 PREC = {"d": 1, "dd": 2, "td": 3, "qd": 4}
 
@@ -68,11 +69,21 @@ def _load():
         "mpspmv_batch_get_plan": [vp, vp, vp],
         "mpspmv_batch_spmm": [vp, vp, vp, vp, vp, vp],
         "mpspmv_batch_cg": [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, vp, vp, vp, vp],
+        "mpspmv_ladder_solve": [vp, c_int, vp, vp, ctypes.c_double, ctypes.c_double, c_int, vp, vp, vp, vp],
+        "mpspmv_cg_history": [vp, vp, c_int, vp, vp],
+        "mpspmv_features": [vp, vp, vp, vp],
+        "mpspmv_mlp_forward": [vp, c_int, vp, c_int, vp, vp],
+        "mpspmv_mlp_grad": [vp, c_int, vp, vp, c_int, vp, vp, vp],
+        "mpspmv_mlp_train": [vp, c_int, vp, vp, c_int, c_int, c_int, ctypes.c_float, vp, vp],
+        "mpspmv_select_precision": [vp, vp, c_int, vp, vp, vp, vp],
+        "mpspmv_solve_auto": [vp, vp, c_int, vp, vp, ctypes.c_double, ctypes.c_double, c_int, vp, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = c_int
+    lib.mpspmv_mlp_param_count.argtypes = [c_int]
+    lib.mpspmv_mlp_param_count.restype = i64
     lib.mpspmv_strerror.argtypes = [c_int]
     lib.mpspmv_strerror.restype = ctypes.c_char_p
     return lib
@@ -228,6 +239,79 @@ def mpspmv_batch_cg(b, B, X, nsys, rtol, atol=0.0, maxit=1000, stream=None):
     if st not in (MPSPMV_OK, MPSPMV_ENOCONV, MPSPMV_EBREAKDOWN):
         raise MpspmvError(st, "mpspmv_batch_cg")
     return st, it, rr, ss
+
+
+def _handles4(hs):
+    return (ctypes.c_void_p * 4)(*[(h.value if isinstance(h, ctypes.c_void_p) else h) if h is not None else None
+                                   for h in hs])
+
+
+def mpspmv_ladder_solve(hs, start_L, b, x, rtol, atol=0.0, maxit=1000, stream=None):
+    """Returns (status, final level, iterations per level, relres)."""
+    fl = ctypes.c_int()
+    it = (ctypes.c_int * 4)()
+    rr = ctypes.c_double()
+    st = _lib.mpspmv_ladder_solve(_handles4(hs), start_L, _ptr(b), _ptr(x), rtol, atol, maxit, ctypes.byref(fl),
+                                  it, ctypes.byref(rr), _stream(stream))
+    if st not in (MPSPMV_OK, MPSPMV_ENOCONV):
+        raise MpspmvError(st, "mpspmv_ladder_solve")
+    return st, fl.value, list(it), rr.value
+
+
+def mpspmv_cg_history(h, b, k=8, stream=None):
+    out = np.zeros(k)
+    _check(_lib.mpspmv_cg_history(h, _ptr(b), k, out.ctypes.data, _stream(stream)), "mpspmv_cg_history")
+    return out
+
+
+def mpspmv_features(h, cg_hist=None, stream=None):
+    f = np.zeros(32, dtype=np.float32)
+    hh = None if cg_hist is None else np.ascontiguousarray(cg_hist, dtype=np.float64)
+    _check(_lib.mpspmv_features(h, None if hh is None else hh.ctypes.data, f.ctypes.data, _stream(stream)),
+           "mpspmv_features")
+    return f
+
+
+def mpspmv_mlp_param_count(C):
+    return int(_lib.mpspmv_mlp_param_count(C))
+
+
+def mpspmv_mlp_forward(params, C, X, B, logits, stream=None):
+    _check(_lib.mpspmv_mlp_forward(_ptr(params), C, _ptr(X), B, _ptr(logits), _stream(stream)), "mpspmv_mlp_forward")
+
+
+def mpspmv_mlp_grad(params, C, X, y, B, grads, stream=None):
+    loss = ctypes.c_float()
+    _check(_lib.mpspmv_mlp_grad(_ptr(params), C, _ptr(X), _ptr(y), B, _ptr(grads), ctypes.byref(loss),
+                                _stream(stream)), "mpspmv_mlp_grad")
+    return loss.value
+
+
+def mpspmv_mlp_train(params, C, X, y, n, batch, epochs, lr, stream=None):
+    losses = np.zeros(max(epochs, 1), dtype=np.float32)
+    _check(_lib.mpspmv_mlp_train(_ptr(params), C, _ptr(X), _ptr(y), n, batch, epochs, ctypes.c_float(lr),
+                                 losses.ctypes.data, _stream(stream)), "mpspmv_mlp_train")
+    return losses[:epochs]
+
+
+def mpspmv_select_precision(hs, params, C, b, stream=None):
+    p = ctypes.c_int()
+    f = np.zeros(32, dtype=np.float32)
+    _check(_lib.mpspmv_select_precision(_handles4(hs), _ptr(params), C, _ptr(b), ctypes.byref(p), f.ctypes.data,
+                                        _stream(stream)), "mpspmv_select_precision")
+    return p.value, f
+
+
+def mpspmv_solve_auto(hs, params, C, b, x, rtol, atol=0.0, maxit=1000, stream=None):
+    """Returns (status, chosen level, final level, iterations per level, relres)."""
+    ch, fl = ctypes.c_int(), ctypes.c_int()
+    it = (ctypes.c_int * 4)()
+    rr = ctypes.c_double()
+    st = _lib.mpspmv_solve_auto(_handles4(hs), _ptr(params), C, _ptr(b), _ptr(x), rtol, atol, maxit,
+                                ctypes.byref(ch), ctypes.byref(fl), it, ctypes.byref(rr), _stream(stream))
+    if st not in (MPSPMV_OK, MPSPMV_ENOCONV):
+        raise MpspmvError(st, "mpspmv_solve_auto")
+    return st, ch.value, fl.value, list(it), rr.value
 
 
 def mpspmv_probe_fp64(op, iters=4096, stream=None):

@@ -106,7 +106,8 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
   *out = nullptr;
   if (nrows < 0 || ncols < 0 || nnz_in < 0 || nrows >= INT32_MAX || ncols >= INT32_MAX) return MPSPMV_EINVAL;
   if (prec < 1 || prec > 4) return MPSPMV_EINVAL;
-  if (flags & ~(MPSPMV_COMPLEX | MPSPMV_MIXED | MPSPMV_SYMMETRIC | MPSPMV_ONE_BASED)) return MPSPMV_EINVAL;
+  if (flags & ~(MPSPMV_COMPLEX | MPSPMV_MIXED | MPSPMV_SYMMETRIC | MPSPMV_ONE_BASED | MPSPMV_EXACT_ACC))
+    return MPSPMV_EINVAL;
   const bool cplx = flags & MPSPMV_COMPLEX, mixed = flags & MPSPMV_MIXED;
   if (mixed && (val_limbs != 1 || prec == 1)) return MPSPMV_EINVAL;
   if (val_limbs < 1 || val_limbs > prec) return MPSPMV_EINVAL;
@@ -212,6 +213,7 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
   h->L = prec;
   h->cplx = cplx;
   h->mixed = mixed;
+  h->exact = (flags & MPSPMV_EXACT_ACC) != 0;
   h->flags = flags;
   h->P = cplx ? 2 * prec : prec;
   h->Pv = mixed ? V : h->P;

@@ -1,0 +1,171 @@
+// fixacc.cuh -- exact fixed-point accumulation of binary64 terms on the
+// integer pipe (GB300-specific alternative to the MP additions of Section 2).
+//
+// GB300 issues binary64 instructions at about 2 per clock per SM and 32-bit
+// integer instructions at 64-128 per clock per SM.  The MP additions of a row
+// sum (Algorithm 1: 11 binary64 operations; the QD sloppy add: 87) are the
+// larger part of the binary64 work, so this path keeps only the error-free
+// products on the binary64 pipe (TwoProd by FMA) and adds the resulting
+// binary64 terms exactly into a fixed-point accumulator on the integer pipe.
+//
+// Accumulator: D signed 64-bit digits, digit j worth 2^(32 j + base); a term
+// (53-bit mantissa at an arbitrary exponent) is split into at most three
+// 32-bit chunks added to three consecutive digits without carry propagation
+// (a digit absorbs 2^31 chunks before it could overflow).  The top digit is
+// head-room: terms are placed so that their top bit lies below digit D-1; a
+// larger term moves the window up by whole digits (carries of the dropped
+// digits are propagated first; what falls below the window is below the
+// format's unit roundoff relative to the largest term).  At the end of a row
+// the carries are propagated once and the value is cut into L binary64
+// components by truncation (value = sum of components to 53 L bits).
+#pragma once
+#include <stdint.h>
+
+namespace mpk {
+
+template <int D>
+struct FixAcc {
+  long long d[D];
+  int base;   // binary exponent of the unit of digit 0
+  bool live;  // a non-zero term has been added
+  bool bad;   // a non-finite term was seen (the result is NaN)
+};
+
+template <int D>
+__device__ __forceinline__ void fa_reset(FixAcc<D>& a) {
+#pragma unroll
+  for (int j = 0; j < D; j++) a.d[j] = 0;
+  a.base = 0;
+  a.live = false;
+  a.bad = false;
+}
+
+// Move the window up by s digits (rare): carries of the dropped digits go up
+// first, the dropped remainders are below the new window.
+template <int D>
+__device__ __forceinline__ void fa_shift_digits(FixAcc<D>& a, int s) {
+  if (s >= D) {
+#pragma unroll
+    for (int j = 0; j < D; j++) a.d[j] = 0;
+    a.base += 32 * s;
+    return;
+  }
+  for (int t = 0; t < s; t++) {
+    const long long c = a.d[0] >> 32;  // floor(d0 / 2^32)
+#pragma unroll
+    for (int j = 0; j < D - 1; j++) a.d[j] = a.d[j + 1];
+    a.d[D - 1] = 0;
+    a.d[0] += c;
+    a.base += 32;
+  }
+}
+
+// a += v exactly (up to the window's lower end)
+template <int D>
+__device__ __forceinline__ void fa_add(FixAcc<D>& a, double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int ef = (int)((bits >> 52) & 0x7ff);
+  unsigned long long m = bits & 0xfffffffffffffULL;
+  if (ef == 0x7ff) {
+    a.bad = true;
+    return;
+  }
+  if (ef) m |= 1ULL << 52;
+  if (m == 0) return;
+  const int e0 = (ef ? ef : 1) - 1075;  // v = +-m * 2^e0
+  if (!a.live) {
+    // place the top bit (at most e0 + 52) in the last bit of digit D-2
+    a.base = e0 + 52 - (32 * (D - 1) - 1);
+    a.live = true;
+  }
+  int pos = e0 - a.base;
+  if (pos + 52 >= 32 * (D - 1)) {
+    fa_shift_digits<D>(a, (pos + 52 - (32 * (D - 1) - 1) + 31) >> 5);
+    pos = e0 - a.base;
+  }
+  if (pos < 0) {
+    if (pos <= -53) return;  // entirely below the window
+    m >>= -pos;              // truncate the part below the window
+    pos = 0;
+  }
+  const int w = pos >> 5, r = pos & 31;
+  const unsigned long long lo = m << r;
+  const unsigned long long hi = r ? (m >> (64 - r)) : 0ULL;
+  long long c0 = (long long)(lo & 0xffffffffULL), c1 = (long long)(lo >> 32), c2 = (long long)hi;
+  if (bits >> 63) {
+    c0 = -c0;
+    c1 = -c1;
+    c2 = -c2;
+  }
+#pragma unroll
+  for (int j = 0; j < D; j++) a.d[j] += (j == w) ? c0 : ((j == w + 1) ? c1 : ((j == w + 2) ? c2 : 0LL));
+}
+
+// bits pos .. pos+63 of the non-negative multi-digit value dig (32-bit digits)
+template <int D>
+__device__ __forceinline__ unsigned long long fa_bits(const unsigned int (&dig)[D], int pos) {
+  unsigned long long r = 0;
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    const int sh = 32 * j - pos;
+    const unsigned long long v = dig[j];
+    if (sh >= 0 && sh < 64) r |= v << sh;
+    else if (sh < 0 && sh > -32) r |= v >> (-sh);
+  }
+  return r;
+}
+
+// Cut the accumulated value into L binary64 components (truncation).
+template <int L, int D>
+__device__ __forceinline__ void fa_to_mp(const FixAcc<D>& a, double* out) {
+#pragma unroll
+  for (int l = 0; l < L; l++) out[l] = 0.0;
+  if (a.bad) {
+    out[0] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
+  if (!a.live) return;
+  long long d[D];
+#pragma unroll
+  for (int j = 0; j < D; j++) d[j] = a.d[j];
+#pragma unroll
+  for (int j = 0; j < D - 1; j++) {
+    const long long c = d[j] >> 32;
+    d[j] -= c << 32;
+    d[j + 1] += c;
+  }
+  const bool neg = d[D - 1] < 0;
+  if (neg) {
+#pragma unroll
+    for (int j = 0; j < D; j++) d[j] = -d[j];
+#pragma unroll
+    for (int j = 0; j < D - 1; j++) {
+      const long long c = d[j] >> 32;
+      d[j] -= c << 32;
+      d[j + 1] += c;
+    }
+  }
+  unsigned int dig[D];
+  int top = -1;
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    dig[j] = (unsigned int)d[j];  // every digit is now in [0, 2^32)
+    if (dig[j]) top = 32 * j + 31 - __clz(dig[j]);
+  }
+  if (top < 0) return;
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    const int lsb = top - 52 - 53 * l;  // component l holds bits lsb .. lsb + 52
+    if (lsb + 52 < 0) break;
+    unsigned long long chunk;
+    if (lsb >= 0) {
+      chunk = fa_bits<D>(dig, lsb) & ((1ULL << 53) - 1);
+    } else {
+      chunk = (fa_bits<D>(dig, 0) << (-lsb)) & ((1ULL << 53) - 1);
+    }
+    const double c = scalbn((double)chunk, lsb + a.base);  // exact: chunk < 2^53
+    out[l] = neg ? -c : c;
+  }
+}
+
+}  // namespace mpk

@@ -46,6 +46,7 @@ struct mpspmv_mat {
   int device;
   int L, P, Pv;  // components, vector planes, stored value planes
   bool cplx, mixed;
+  bool exact = false;  // MPSPMV_EXACT_ACC: products on the binary64 pipe, exact integer accumulation
   unsigned flags;
   int64_t nrows, ncols, nnz, max_row_nnz;
   int32_t K;

@@ -13,4 +13,5 @@ struct KrylovState {
   double bnorm;   // ||b||_2 (binary64)
   double relres;  // ||b - A x|| / ||b|| at exit
   double sc[8][8];  // MP scalars: [slot][0..3] real components, [4..7] imaginary components
+  double hist[16];  // CG: ||r_k|| / ||b|| (recurrence residual) for k = 1..16
 };

@@ -72,7 +72,7 @@ __global__ void build_tiles_kernel(DevMat m, int32_t* __restrict__ cols_out, dou
 // Carry layout: carry[((w*P + p)*nchunks + c)*kc + rhs], w = 0 first-row
 // partial, w = 1 last-row partial.
 // ---------------------------------------------------------------------------
-template <int L, bool CPLX, bool MIXED>
+template <int L, bool CPLX, bool MIXED, bool EXACT>
 __global__ void __launch_bounds__(kThreads) spmv_runs_kernel(DevMat m, const double* __restrict__ x, int64_t xs,
                                                              int64_t xoff, double* __restrict__ y, int64_t ys,
                                                              int64_t yoff, double* __restrict__ carry, int kc,
@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(kThreads) spmv_runs_kernel(DevMat m, const dou
   const int64_t c = t / kp;
   const int rhs = (int)(t - c * kp);
   if (c >= m.nchunks || rhs >= k) return;
-  process_run<L, CPLX, MIXED>(m, c, rhs, x, xs, xoff, y, ys, yoff, carry, kc);
+  if (EXACT) process_run_exact<L, CPLX, MIXED>(m, c, rhs, x, xs, xoff, y, ys, yoff, carry, kc);
+  else process_run<L, CPLX, MIXED>(m, c, rhs, x, xs, xoff, y, ys, yoff, carry, kc);
 }
 
 // Rows cut by run boundaries: partial of the run where the row starts (slot
@@ -220,8 +221,12 @@ int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, d
   while (kp < k) kp <<= 1;
   const int64_t threads = h->nchunks * kp;
   const int64_t blocks = (threads + kThreads - 1) / kThreads;
-  spmv_runs_kernel<L, CPLX, MIXED><<<(unsigned)blocks, kThreads, 0, s>>>(m, x, xs, xoff, y, ys, yoff, h->d_carry,
-                                                                        h->carry_k, kp, k, gate);
+  if (h->exact)
+    spmv_runs_kernel<L, CPLX, MIXED, true><<<(unsigned)blocks, kThreads, 0, s>>>(m, x, xs, xoff, y, ys, yoff,
+                                                                              h->d_carry, h->carry_k, kp, k, gate);
+  else
+    spmv_runs_kernel<L, CPLX, MIXED, false><<<(unsigned)blocks, kThreads, 0, s>>>(m, x, xs, xoff, y, ys, yoff,
+                                                                               h->d_carry, h->carry_k, kp, k, gate);
   MPS_CUDA(cudaGetLastError());
   if (h->nshort > 0) {
     const int64_t ct = h->nshort * k;

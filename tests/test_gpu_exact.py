@@ -1,0 +1,143 @@
+"""The exact-accumulation arithmetic (MPSPMV_EXACT_ACC): error-free products
+on the binary64 pipe, exact fixed-point row sums on the integer pipe.  It
+must meet the same componentwise bound 8 m u (|A||x|)_i as the paper-order
+arithmetic against the exact value (it is not bit-identical to it)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import exact
+from tests._util import csr_pair, gpu_spmv, to_dev
+
+pytestmark = pytest.mark.gpu
+
+mps = pytest.importorskip("paper_2412_17510_gb300")
+torch = pytest.importorskip("torch")
+
+EX = 16  # MPSPMV_EXACT_ACC
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_full_limb_random_within_bound(L, cplx):
+    coo = workloads.random_sparse(600, 500, 40, seed=10 + L, cplx=cplx, L=L, full_limb=True, empty_frac=0.1)
+    A, h = csr_pair(coo, L, vals=coo.val, flags=EX | (1 if cplx else 0))
+    try:
+        x = workloads.full_limb_vector(500, L, seed=3, cplx=cplx)
+        y = gpu_spmv(h, x, A.P, 600)
+        assert exact.bound_ratio(y, A, x) <= 1.0
+        empty = np.diff(A.indptr) == 0
+        assert not y[:, empty].any()
+    finally:
+        mps.mpspmv_destroy(h)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_mixed_mode_within_bound(L, cplx):
+    coo = workloads.random_sparse(400, 400, 30, seed=4, cplx=cplx)
+    Ap = oracle.coo_to_csr(400, 400, coo.row, coo.col, coo.promoted(L), L, cplx)
+    h = mps.mpspmv_create_csr(400, 400, coo.row, coo.col, coo.val, L, EX | mps.MPSPMV_MIXED | (1 if cplx else 0),
+                              val_limbs=1)
+    try:
+        x = workloads.full_limb_vector(400, L, seed=3, cplx=cplx)
+        y = gpu_spmv(h, x, Ap.P, 400)
+        assert exact.bound_ratio(y, Ap, x) <= 1.0
+    finally:
+        mps.mpspmv_destroy(h)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_integer_matrices_bit_exact(L, cplx):
+    coo = workloads.integer_matrix(300, 280, 0.05, seed=L, cplx=cplx)
+    A, h = csr_pair(coo, L, flags=EX | (1 if cplx else 0))
+    try:
+        x = workloads.integer_vector(280, L, seed=7, cplx=cplx)
+        y = gpu_spmv(h, x, A.P, 300)
+        assert np.array_equal(y, oracle.spmv(A, x))
+    finally:
+        mps.mpspmv_destroy(h)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_wide_exponent_range_and_long_rows(L):
+    """Rows whose products span 2^-900 .. 2^900 (the accumulation window has
+    to move up several times) and rows spanning many runs."""
+    rng = np.random.default_rng(5)
+    n, m = 64, 300
+    ncol = 512
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        k = m if i % 8 == 0 else 20
+        c = np.sort(rng.choice(ncol, k, replace=False))
+        v = rng.standard_normal(k) * 2.0 ** rng.integers(-450, 450, k)
+        rows.append(np.full(k, i)); cols.append(c); vals.append(v)
+    coo = workloads.COO(n, ncol, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)[None, :])
+    A, h = csr_pair(coo, L, flags=EX)
+    try:
+        x = workloads.full_limb_vector(ncol, L, seed=9)
+        x[:, ::3] *= 2.0 ** 400
+        y = gpu_spmv(h, x, L, n)
+        assert exact.bound_ratio(y, A, x) <= 1.0
+    finally:
+        mps.mpspmv_destroy(h)
+
+
+def test_non_finite_x_gives_nan_rows():
+    coo = workloads.laplacian_2d(8)
+    A, h = csr_pair(coo, 2, flags=EX)
+    try:
+        x = workloads.full_limb_vector(64, 2, seed=1)
+        x[0, 10] = np.inf
+        y = gpu_spmv(h, x, 2, 64)
+        bad_rows = [i for i in range(64) if 10 in A.indices[A.indptr[i]:A.indptr[i + 1]]]
+        assert all(np.isnan(y[0, i]) for i in bad_rows)
+        good = [i for i in range(64) if i not in bad_rows]
+        assert np.isfinite(y[:, good]).all()
+    finally:
+        mps.mpspmv_destroy(h)
+
+
+def test_spmm_and_batch_equal_spmv():
+    L = 4
+    coo = workloads.random_sparse(500, 500, 30, seed=6, L=L, full_limb=True)
+    A, h = csr_pair(coo, L, vals=coo.val, flags=EX)
+    try:
+        k = 5
+        X = np.stack([workloads.full_limb_vector(500, L, seed=20 + c) for c in range(k)], axis=-1)
+        Xd = to_dev(X)
+        Yd = torch.empty((L, 500, k), dtype=torch.float64, device="cuda")
+        mps.mpspmv_spmm(h, k, Xd, k, Yd, k)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().numpy()
+        for c in range(k):
+            assert np.array_equal(Y[:, :, c], gpu_spmv(h, X[:, :, c], L, 500))
+        b = mps.mpspmv_batch_create([h], [k], 0)
+        try:
+            Yb = torch.empty_like(Yd)
+            mps.mpspmv_batch_spmm(b, [Xd], [Yb])
+            torch.cuda.synchronize()
+            assert np.array_equal(Yb.cpu().numpy(), Y)
+        finally:
+            mps.mpspmv_batch_destroy(b)
+    finally:
+        mps.mpspmv_destroy(h)
+
+
+def test_stencil_full_size_sampled_rows():
+    """27-point stencil 64^3 (n = 262,144), DD and QD, exact accumulation vs
+    the paper-order arithmetic: both within the bound on sampled rows."""
+    coo = workloads.stencil_27pt(64)
+    rows = list(range(0, coo.nrows, 4099))
+    for L in (2, 4):
+        A = oracle.coo_to_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.promoted(L), L)
+        x = workloads.full_limb_vector(coo.ncols, L, seed=0)
+        for flags in (0, EX):
+            h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, flags, val_limbs=1)
+            try:
+                y = gpu_spmv(h, x, L, coo.nrows)
+                assert exact.bound_ratio(y[:, rows], A, x, rows=rows) <= 1.0
+            finally:
+                mps.mpspmv_destroy(h)

@@ -47,7 +47,7 @@ def spd_system(L, nx=12, ny=10, grade=0.0, seed=0):
     rng = np.random.default_rng(seed)
     if grade:
         d = 10.0 ** rng.uniform(-grade, grade, n)
-        coo = workloads.COO(n, n, coo.row, coo.col, (coo.val[0] * d[coo.row] * d[coo.col])[None, :])
+        coo = workloads.COO(n, n, coo.row, coo.col, (coo.val[0] * (d[coo.row] * d[coo.col]))[None, :])
     b = np.zeros((L, n))
     b[0] = rng.uniform(-1, 1, n)
     return coo, b

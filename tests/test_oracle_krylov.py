@@ -94,7 +94,7 @@ def test_cg_iteration_counts_do_not_grow_with_precision():
     its = []
     for L in (2, 3, 4):
         # D A D with a graded diagonal scaling: SPD, condition ~1e9
-        v = coo.val[0] * scale[coo.row] * scale[coo.col]
+        v = coo.val[0] * (scale[coo.row] * scale[coo.col])   # exactly symmetric
         vv = np.zeros((L, coo.nnz)); vv[0] = v
         A = oracle.coo_to_csr(n, n, coo.row, coo.col, vv, L)
         b = np.zeros((L, n)); b[0] = 1.0

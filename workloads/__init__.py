@@ -298,7 +298,8 @@ def random_sparse(nrows, ncols, row_len_max, seed=0, cplx=False, L=1, full_limb=
 
 
 def selector_system(n, log10_cond, seed=0, nnz_range=(8, 24)):
-    """SPD system A = D (L L^T + I) D for the precision selector: L unit lower
+    """SPD system A = D (L L^T + I) D for the precision selector (stored
+    exactly symmetric): L unit lower
     triangular with U{nnz_range} off-diagonal entries per row (positions
     uniform in [0, i), values N(0,1)); D = diag(10^t_i) with t_i graded
     linearly over the rows so that cond(A) is about 10^log10_cond (cond(L L^T
@@ -321,7 +322,10 @@ def selector_system(n, log10_cond, seed=0, nnz_range=(8, 24)):
     M = (Lm @ Lm.T + sp.identity(n)).tocsr()
     tau = max(0.0, (log10_cond - 2.0) / 2.0)
     d = 10.0 ** (tau * np.arange(n) / max(n - 1, 1))
-    A = (sp.diags(d) @ M @ sp.diags(d)).tocoo()
+    A = (sp.diags(d) @ M @ sp.diags(d)).tocsr()
+    # the products round a_ij and a_ji differently; averaging the two makes the
+    # stored binary64 matrix exactly symmetric (fl(u + v) = fl(v + u))
+    A = ((A + A.T) * 0.5).tocoo()
     order = np.lexsort((A.col, A.row))
     coo = COO(n, n, A.row[order], A.col[order], A.data[order][None, :], "selector_n%d_c%g" % (n, log10_cond))
     b = rng.uniform(-1.0, 1.0, n)

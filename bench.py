@@ -42,6 +42,10 @@ PNAME = {1: "D", 2: "DD", 3: "TD", 4: "QD"}
 # (Algorithms 2 + 1 for DD; QD sloppy mul + add; TD = QD with zero fourth
 # components plus one folding addition each) -- the oracle's operation counts.
 OPS_PER_ENTRY = {2: 9 + 11, 3: 124 + 88, 4: 123 + 87}
+# exact accumulation (MPSPMV_EXACT_ACC): binary64 instructions per stored entry
+# of the product stage (TwoProd = DMUL + DFMA; FMA chains for the rounded
+# terms); the row sums run on the integer pipe.
+OPS_PER_ENTRY_EXACT = {2: 4, 3: 9, 4: 16}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -112,7 +116,7 @@ class ClockSampler:
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("spmv.cu", "mp_arith.cuh"):
+    for f in ("spmv.cu", "mp_arith.cuh", "run_body.cuh", "fixacc.cuh"):
         with open(os.path.join(ROOT, "paper_2412_17510_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -387,9 +391,10 @@ def main():
     ap.add_argument("--small", action="store_true", help="reduced matrices (development)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg")
     ap.add_argument("--only", default=None, help="run one variant, e.g. powerlaw_1e5/QD (profiling)")
-    ap.add_argument("--arith", default="paper", choices=["paper", "exact"],
+    ap.add_argument("--arith", default="both", choices=["paper", "exact", "both"],
                     help="paper: the paper's DD/TD/QD operation sequences; exact: error-free products on the "
-                         "binary64 pipe with exact integer accumulation (MPSPMV_EXACT_ACC)")
+                         "binary64 pipe with exact integer accumulation (MPSPMV_EXACT_ACC); both: value from "
+                         "exact, the paper-order step timed too")
     ap.add_argument("--suite", action="store_true",
                     help="also measure the complex, batched and selector workloads (adds minutes)")
     args = ap.parse_args()
@@ -417,20 +422,24 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     mats = make_matrices(args.small)
-    variants = []
+    ariths = ["exact", "paper"] if args.arith == "both" else [args.arith]
+    sets = {ar: [] for ar in ariths}
     xs_host = {}
+    xs_dev = {}
     for mname, coo in mats.items():
         xs_host[mname] = {L: workloads.full_limb_vector(coo.ncols, L, seed=0) for L in PRECS}
         for L in PRECS:
             if args.only and args.only != "%s/%s" % (mname, PNAME[L]):
                 continue
-            fl = mps.MPSPMV_EXACT_ACC if args.arith == "exact" else 0
-            h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, fl, val_limbs=1)
-            info = mps.mpspmv_get_info(h)
             x = torch.from_numpy(xs_host[mname][L]).cuda()
             y = torch.empty((L, coo.nrows), dtype=torch.float64, device="cuda")
-            variants.append(dict(name="%s/%s" % (mname, PNAME[L]), m=mname, L=L, h=h, x=x, y=y, info=info,
-                                 nnz=info["nnz"], nrows=coo.nrows, ncols=coo.ncols))
+            xs_dev[(mname, L)] = x
+            for ar in ariths:
+                fl = mps.MPSPMV_EXACT_ACC if ar == "exact" else 0
+                h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, fl, val_limbs=1)
+                info = mps.mpspmv_get_info(h)
+                sets[ar].append(dict(name="%s/%s" % (mname, PNAME[L]), m=mname, L=L, h=h, x=x, y=y, info=info,
+                                     nnz=info["nnz"], nrows=coo.nrows, ncols=coo.ncols, arith=ar))
     torch.cuda.synchronize()
 
     fp64_fma = mps.mpspmv_probe_fp64(0)
@@ -438,7 +447,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(evs=None):
+    def step(variants, evs=None):
         for i, v in enumerate(variants):
             if evs:
                 evs[i][0].record(stream)
@@ -446,36 +455,40 @@ def main():
             if evs:
                 evs[i][1].record(stream)
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
+    def timed(variants, sample_clocks):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(variants)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        all_evs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in variants]
+            step(variants, evs)
+            all_evs.append(evs)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = sampler.stop() if sampler else None
+        per_var = np.zeros(len(variants))
+        step_ms = []
+        for evs in all_evs:
+            t = [a.elapsed_time(b) for a, b in evs]
+            per_var += np.array(t)
+            step_ms.append(sum(t))
+        return per_var / args.steps, float(np.mean(step_ms)), clk
 
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    all_evs = []
-    for _ in range(args.steps):
-        flush.zero_()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in variants]
-        step(evs)
-        all_evs.append(evs)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-
-    per_var = np.zeros(len(variants))
-    step_ms = []
-    for evs in all_evs:
-        t = [a.elapsed_time(b) for a, b in evs]
-        per_var += np.array(t)
-        step_ms.append(sum(t))
-    per_var /= args.steps
-    ms = float(np.mean(step_ms))
+    primary = ariths[0]
+    variants = sets[primary]
+    per_var, ms, clocks = timed(variants, True)
+    other = {ar: timed(sets[ar], False) for ar in ariths[1:]}
     if dist:
         tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -505,17 +518,33 @@ def main():
             e2e_ms.append((t1 - t0) * 1e3)
     e2e_value = step_nnz * world / (np.mean(e2e_ms) * 1e-3) / 1e9
 
-    # roofline of the dominant kernel (largest share of the step)
-    dom = int(np.argmax(per_var))
-    v = variants[dom]
-    t_s = per_var[dom] * 1e-3
-    ops = v["nnz"] * OPS_PER_ENTRY[v["L"]]
-    byts = algorithmic_bytes(v["nnz"], v["nrows"], v["ncols"], v["L"])
     hbm = 6786.2
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except Exception:
         pass
+
+    def ops_of(v):
+        table = OPS_PER_ENTRY_EXACT if v["arith"] == "exact" else OPS_PER_ENTRY
+        return v["nnz"] * table[v["L"]]
+
+    def breakdown_of(vs, pv):
+        out = {}
+        for i, w in enumerate(vs):
+            t = pv[i] * 1e-3
+            o = ops_of(w)
+            b = algorithmic_bytes(w["nnz"], w["nrows"], w["ncols"], w["L"])
+            troof = max(o / fp64_fma, b / (hbm * 1e9))
+            out[w["name"]] = {"ms": pv[i], "gnnz_s": w["nnz"] / t / 1e9, "roofline_frac": troof / t,
+                              "fp64_tinstr_s": o / t / 1e12, "hbm_gbs": b / t / 1e9, "chunk": w["info"]["chunk"]}
+        return out
+
+    # roofline of the dominant kernel (largest share of the step)
+    dom = int(np.argmax(per_var))
+    v = variants[dom]
+    t_s = per_var[dom] * 1e-3
+    ops = ops_of(v)
+    byts = algorithmic_bytes(v["nnz"], v["nrows"], v["ncols"], v["L"])
     t_alu = ops / fp64_fma
     t_hbm = byts / (hbm * 1e9)
     bound = "alu" if t_alu >= t_hbm else "hbm"
@@ -524,20 +553,19 @@ def main():
     else:
         achieved, peak, unit = byts / t_s / 1e9, hbm, "GB/s"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-            "traffic": stored_traffic(v["name"]), "kernel": "spmv_runs_kernel + combine_kernel, " + v["name"],
+            "traffic": stored_traffic(v["arith"] + ":" + v["name"]),
+            "kernel": "spmv_runs_kernel + combine kernels, %s arithmetic, %s" % (v["arith"], v["name"]),
             "peak_source": "measured in this run by mpspmv_probe_fp64 (DFMA chains, all SMs)"
             if bound == "alu" else "MEASURED_PEAKS.json hbm_gbs",
             "algorithmic_ops_per_launch": ops, "algorithmic_bytes_per_launch": byts,
-            "fp64_dadd_peak_tinstr_s": fp64_add / 1e12}
-
-    breakdown = {}
-    for i, w in enumerate(variants):
-        t = per_var[i] * 1e-3
-        o = w["nnz"] * OPS_PER_ENTRY[w["L"]]
-        b = algorithmic_bytes(w["nnz"], w["nrows"], w["ncols"], w["L"])
-        troof = max(o / fp64_fma, b / (hbm * 1e9))
-        breakdown[w["name"]] = {"ms": per_var[i], "gnnz_s": w["nnz"] / t / 1e9, "roofline_frac": troof / t,
-                                "fp64_tinstr_s": o / t / 1e12, "hbm_gbs": b / t / 1e9, "chunk": w["info"]["chunk"]}
+            "fp64_dadd_peak_tinstr_s": fp64_add / 1e12,
+            "ops_per_entry": (OPS_PER_ENTRY_EXACT if v["arith"] == "exact" else OPS_PER_ENTRY)[v["L"]]}
+    breakdown = breakdown_of(variants, per_var)
+    other_out = {}
+    for ar, (pv, oms, _) in other.items():
+        onnz = sum(w["nnz"] for w in sets[ar])
+        other_out[ar] = {"value": onnz / (oms * 1e-3) / 1e9, "ms_per_step": oms,
+                         "breakdown": breakdown_of(sets[ar], pv)}
 
     cpu = None
     if pool is not None:
@@ -551,8 +579,9 @@ def main():
                "wall_s": time.perf_counter() - t0}
         pool.close()
 
-    for w in variants:
-        mps.mpspmv_destroy(w["h"])
+    for ar in ariths:
+        for w in sets[ar]:
+            mps.mpspmv_destroy(w["h"])
     suite = None
     if args.suite and rank == 0:
         del flush
@@ -568,8 +597,10 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "fp64_peak_tinstr_s": {"dfma": fp64_fma / 1e12, "dadd": fp64_add / 1e12},
-            "breakdown": breakdown,
+            "arith": primary, "breakdown": breakdown,
         }
+        if other_out:
+            line["other_arith"] = other_out
         if suite is not None:
             line["suite"] = suite
         print(json.dumps(line))

@@ -46,6 +46,9 @@ OPS_PER_ENTRY = {2: 9 + 11, 3: 124 + 88, 4: 123 + 87}
 # of the product stage (TwoProd = DMUL + DFMA; FMA chains for the rounded
 # terms); the row sums run on the integer pipe.
 OPS_PER_ENTRY_EXACT = {2: 4, 3: 9, 4: 16}
+# ... and on binary64 data (only leading components stored; MP x binary64
+# product forms, the omitted products being exactly zero): 2L - 1
+OPS_PER_ENTRY_EXACT_D = {2: 3, 3: 5, 4: 7}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -55,11 +58,13 @@ def make_matrices(small=False):
     return {"stencil27_128^3": workloads.stencil_27pt(128), "powerlaw_1e6_zipf1.5": workloads.power_law(1000000)}
 
 
-def algorithmic_bytes(nnz, nrows, ncols, L):
+def algorithmic_bytes(nnz, nrows, ncols, L, value_planes=None):
     """Compulsory HBM traffic of one SpMV: per entry a 4-byte column index and
-    L value components; per row its start offset and the L result components;
-    x read once (L components per column)."""
-    return nnz * (4 + 8 * L) + nrows * (8 + 8 * L) + ncols * 8 * L
+    its stored value components (L, or 1 when only leading components are
+    stored); per row its start offset and the L result components; x read
+    once (L components per column)."""
+    vp = L if value_planes is None else value_planes
+    return nnz * (4 + 8 * vp) + nrows * (8 + 8 * L) + ncols * 8 * L
 
 
 # ---------------------------------------------------------------------------
@@ -524,16 +529,23 @@ def main():
     except Exception:
         pass
 
+    def table_of(v):
+        if v["arith"] != "exact":
+            return OPS_PER_ENTRY
+        return OPS_PER_ENTRY_EXACT_D if v["info"]["value_planes"] == 1 else OPS_PER_ENTRY_EXACT
+
     def ops_of(v):
-        table = OPS_PER_ENTRY_EXACT if v["arith"] == "exact" else OPS_PER_ENTRY
-        return v["nnz"] * table[v["L"]]
+        return v["nnz"] * table_of(v)[v["L"]]
+
+    def bytes_of(v):
+        return algorithmic_bytes(v["nnz"], v["nrows"], v["ncols"], v["L"], v["info"]["value_planes"])
 
     def breakdown_of(vs, pv):
         out = {}
         for i, w in enumerate(vs):
             t = pv[i] * 1e-3
             o = ops_of(w)
-            b = algorithmic_bytes(w["nnz"], w["nrows"], w["ncols"], w["L"])
+            b = bytes_of(w)
             troof = max(o / fp64_fma, b / (hbm * 1e9))
             out[w["name"]] = {"ms": pv[i], "gnnz_s": w["nnz"] / t / 1e9, "roofline_frac": troof / t,
                               "fp64_tinstr_s": o / t / 1e12, "hbm_gbs": b / t / 1e9, "chunk": w["info"]["chunk"]}
@@ -544,7 +556,7 @@ def main():
     v = variants[dom]
     t_s = per_var[dom] * 1e-3
     ops = ops_of(v)
-    byts = algorithmic_bytes(v["nnz"], v["nrows"], v["ncols"], v["L"])
+    byts = bytes_of(v)
     t_alu = ops / fp64_fma
     t_hbm = byts / (hbm * 1e9)
     bound = "alu" if t_alu >= t_hbm else "hbm"
@@ -559,7 +571,7 @@ def main():
             if bound == "alu" else "MEASURED_PEAKS.json hbm_gbs",
             "algorithmic_ops_per_launch": ops, "algorithmic_bytes_per_launch": byts,
             "fp64_dadd_peak_tinstr_s": fp64_add / 1e12,
-            "ops_per_entry": (OPS_PER_ENTRY_EXACT if v["arith"] == "exact" else OPS_PER_ENTRY)[v["L"]]}
+            "ops_per_entry": table_of(v)[v["L"]], "value_planes": v["info"]["value_planes"]}
     breakdown = breakdown_of(variants, per_var)
     other_out = {}
     for ar, (pv, oms, _) in other.items():

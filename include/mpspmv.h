@@ -76,6 +76,8 @@ typedef struct {
   uint32_t flags;
   int64_t device_bytes; /* device memory owned by the handle */
   int64_t nlong_rows;   /* of nsplit_rows, those spanning more than 32 runs */
+  int64_t value_planes; /* binary64 value planes stored per entry (1 or 2 when only leading
+                           components are kept: M mode, or MPSPMV_EXACT_ACC on binary64 data) */
 } mpspmv_info;
 
 /*

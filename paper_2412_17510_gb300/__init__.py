@@ -42,7 +42,8 @@ class mpspmv_info(ctypes.Structure):
     _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("max_row_nnz", ctypes.c_int64), ("nchunks", ctypes.c_int64), ("nsplit_rows", ctypes.c_int64),
                 ("prec", ctypes.c_int32), ("planes", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("device_bytes", ctypes.c_int64), ("nlong_rows", ctypes.c_int64)]
+                ("flags", ctypes.c_uint32), ("device_bytes", ctypes.c_int64), ("nlong_rows", ctypes.c_int64),
+                ("value_planes", ctypes.c_int64)]
 
 
 def _load():

@@ -214,9 +214,14 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
   h->cplx = cplx;
   h->mixed = mixed;
   h->exact = (flags & MPSPMV_EXACT_ACC) != 0;
+  // Exact accumulation of binary64 data (one value component, no duplicates
+  // to sum): every product of a zero lower component is exactly zero, so
+  // storing the leading components only and using the MP x binary64 product
+  // forms gives the same bits with less work and fewer bytes.
+  h->dstore = h->exact && !mixed && val_limbs == 1 && !dups && prec > 1;
   h->flags = flags;
   h->P = cplx ? 2 * prec : prec;
-  h->Pv = mixed ? V : h->P;
+  h->Pv = (mixed || h->dstore) ? V : h->P;
   h->nrows = nrows;
   h->ncols = ncols;
   h->nnz = nnz;
@@ -286,7 +291,7 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
           goto fail;
         }
       }
-      TRY(mps_build_tiles(h, d_vin, nin, mixed ? 1 : val_limbs, d_runs, d_col, s));
+      TRY(mps_build_tiles(h, d_vin, nin, (mixed || h->dstore) ? 1 : val_limbs, d_runs, d_col, s));
       if (cudaStreamSynchronize(s) != cudaSuccess) {
         st = MPSPMV_ECUDA;
         goto fail;
@@ -360,6 +365,7 @@ int mpspmv_get_info(mpspmv_h h, mpspmv_info* info) {
   info->flags = h->flags;
   info->device_bytes = h->device_bytes;
   info->nlong_rows = h->nsplit - h->nshort;
+  info->value_planes = h->Pv;
   return MPSPMV_OK;
 }
 

@@ -65,7 +65,7 @@ __device__ __forceinline__ int find_entry(const int64_t* __restrict__ start, int
   return lo;
 }
 
-template <int L, bool EXACT>
+template <int L, bool EXACT, bool DSTORE>
 __global__ void __launch_bounds__(kBT) batch_runs_kernel(const BatchEntry* __restrict__ E,
                                                          const int64_t* __restrict__ istart, int nm, int64_t total,
                                                          unsigned long long* __restrict__ head,
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kBT) batch_runs_kernel(const BatchEntry* __res
     const int rhs = b * w + (lane & (w - 1));
     if (c < be->m.nchunks && rhs < k && (!sys_status || sys_status[be->sys0 + rhs] == 0)) {
       if (EXACT)
-        process_run_exact<L, false, false>(be->m, c, rhs, be->X, be->m.ncols * be->ldx, be->ldx, be->Y,
+        process_run_exact<L, false, DSTORE, kBT>(be->m, c, rhs, be->X, be->m.ncols * be->ldx, be->ldx, be->Y,
                                            be->m.nrows * be->ldy, be->ldy, be->carry, be->kc);
       else
         process_run<L, false, false>(be->m, c, rhs, be->X, be->m.ncols * be->ldx, be->ldx, be->Y,
@@ -430,12 +430,15 @@ int layout(mpspmv_batch* b, cudaStream_t s) {
 template <int L>
 int enqueue_spmm(mpspmv_batch* b, const int* sys_status, cudaStream_t s) {
   MPS_CUDA(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long), s));
-  if (b->mats[0]->exact)
-    batch_runs_kernel<L, true><<<b->grid_runs, kBT, 0, s>>>(b->d_entries, b->d_item_start, b->count,
-                                                            b->total_items, b->d_head, sys_status);
+  if (b->mats[0]->exact && b->mats[0]->dstore)
+    batch_runs_kernel<L, true, true><<<b->grid_runs, kBT, 0, s>>>(b->d_entries, b->d_item_start, b->count,
+                                                                  b->total_items, b->d_head, sys_status);
+  else if (b->mats[0]->exact)
+    batch_runs_kernel<L, true, false><<<b->grid_runs, kBT, 0, s>>>(b->d_entries, b->d_item_start, b->count,
+                                                                   b->total_items, b->d_head, sys_status);
   else
-    batch_runs_kernel<L, false><<<b->grid_runs, kBT, 0, s>>>(b->d_entries, b->d_item_start, b->count,
-                                                             b->total_items, b->d_head, sys_status);
+    batch_runs_kernel<L, false, false><<<b->grid_runs, kBT, 0, s>>>(b->d_entries, b->d_item_start, b->count,
+                                                                    b->total_items, b->d_head, sys_status);
   MPS_CUDA(cudaGetLastError());
   if (b->total_comb > 0) {
     batch_combine_kernel<L><<<(unsigned)((b->total_comb + kBT - 1) / kBT), kBT, 0, s>>>(
@@ -731,7 +734,7 @@ int mpspmv_batch_create(const mpspmv_h* mats, const int* k, int count, unsigned 
   for (int i = 0; i < count; i++) {
     const mpspmv_mat* h = mats[i];
     if (!h || h->L != L || h->cplx || h->mixed || h->nnz == 0 || k[i] < 1 || k[i] > 32 ||
-        h->exact != mats[0]->exact)
+        h->exact != mats[0]->exact || h->dstore != mats[0]->dstore)
       return MPSPMV_EINVAL;
   }
   cudaStream_t s = mps_stream(stream);
@@ -755,16 +758,17 @@ int mpspmv_batch_create(const mpspmv_h* mats, const int* k, int count, unsigned 
   }
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  const bool ex = mats[0]->exact;
-  switch (L * 2 + (ex ? 1 : 0)) {
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_runs_kernel<1, false>, kBT, 0); break;
-    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_runs_kernel<1, true>, kBT, 0); break;
-    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_runs_kernel<2, false>, kBT, 0); break;
-    case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_runs_kernel<2, true>, kBT, 0); break;
-    case 6: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_runs_kernel<3, false>, kBT, 0); break;
-    case 7: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_runs_kernel<3, true>, kBT, 0); break;
-    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_runs_kernel<4, false>, kBT, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_runs_kernel<4, true>, kBT, 0); break;
+  const bool ex = mats[0]->exact, ds = mats[0]->dstore;
+  auto occ = [&](auto kern) { cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kBT, 0); };
+  switch (L) {
+    case 1: ex ? (ds ? occ(batch_runs_kernel<1, true, true>) : occ(batch_runs_kernel<1, true, false>))
+               : occ(batch_runs_kernel<1, false, false>); break;
+    case 2: ex ? (ds ? occ(batch_runs_kernel<2, true, true>) : occ(batch_runs_kernel<2, true, false>))
+               : occ(batch_runs_kernel<2, false, false>); break;
+    case 3: ex ? (ds ? occ(batch_runs_kernel<3, true, true>) : occ(batch_runs_kernel<3, true, false>))
+               : occ(batch_runs_kernel<3, false, false>); break;
+    default: ex ? (ds ? occ(batch_runs_kernel<4, true, true>) : occ(batch_runs_kernel<4, true, false>))
+                : occ(batch_runs_kernel<4, false, false>); break;
   }
   b->grid_runs = std::max(1, sms * std::max(per, 1));
   if ((flags & MPSPMV_BATCH_AUTOTUNE) && (st = autotune(b, s))) {

@@ -169,3 +169,116 @@ __device__ __forceinline__ void fa_to_mp(const FixAcc<D>& a, double* out) {
 }
 
 }  // namespace mpk
+
+// ---------------------------------------------------------------------------
+// Shared-memory digit storage.  Registers cannot be indexed by a run-time
+// digit number, so the register accumulator above updates every digit with
+// selects (about 8 D integer instructions per term).  Here the digits of the
+// thread live in shared memory, digit j of thread t at d[j * T + t] (a
+// warp's lanes hit consecutive addresses for any digit numbers), and a term
+// costs three read-modify-writes of the digits it touches.  Positive and
+// negative terms go to separate non-negative digit arrays (the sign selects
+// the array instead of negating three chunks); the flush subtracts them.
+// ---------------------------------------------------------------------------
+namespace mpk {
+
+template <int D, int T>
+struct FixAccS {
+  unsigned long long* dp;  // this thread's digit 0 of the positive terms; digit j at dp[j * T]
+  unsigned long long* dn;  // ... of the negative terms
+  int base;
+  bool live;
+  bool bad;
+};
+
+template <int D, int T>
+__device__ __forceinline__ void fas_reset(FixAccS<D, T>& a) {
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    a.dp[j * T] = 0;
+    a.dn[j * T] = 0;
+  }
+  a.base = 0;
+  a.live = false;
+  a.bad = false;
+}
+
+// Move the window up by s digits (rare; out of line so that the per-term
+// path stays small): carries of the dropped digits go up first.
+template <int D, int T>
+__device__ __noinline__ void fas_shift_smem(unsigned long long* d, int s) {
+  if (s >= D) {
+#pragma unroll
+    for (int j = 0; j < D; j++) d[j * T] = 0;
+    return;
+  }
+  for (int t = 0; t < s; t++) {
+    const unsigned long long c = d[0] >> 32;
+#pragma unroll
+    for (int j = 0; j < D - 1; j++) d[j * T] = d[(j + 1) * T];
+    d[(D - 1) * T] = 0;
+    d[0] += c;
+  }
+}
+
+// a += v (neg: a -= v)
+template <int D, int T>
+__device__ __forceinline__ void fas_add(FixAccS<D, T>& a, double v, bool neg) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int ef = (int)((bits >> 52) & 0x7ff);
+  unsigned long long m = bits & 0xfffffffffffffULL;
+  if (ef == 0x7ff) {
+    a.bad = true;
+    return;
+  }
+  if (ef) m |= 1ULL << 52;
+  if (m == 0) return;
+  const int e0 = (ef ? ef : 1) - 1075;
+  if (!a.live) {
+    a.base = e0 + 52 - (32 * (D - 1) - 1);
+    a.live = true;
+  }
+  int pos = e0 - a.base;
+  if (pos + 52 >= 32 * (D - 1)) {
+    const int sd = (pos + 52 - (32 * (D - 1) - 1) + 31) >> 5;
+    fas_shift_smem<D, T>(a.dp, sd);
+    fas_shift_smem<D, T>(a.dn, sd);
+    a.base += 32 * sd;
+    pos = e0 - a.base;
+  }
+  if (pos < 0) {
+    if (pos <= -53) return;
+    m >>= -pos;
+    pos = 0;
+  }
+  const int w = pos >> 5, r = pos & 31;
+  const unsigned long long lo = m << r;
+  const unsigned long long hi = r ? (m >> (64 - r)) : 0ULL;
+  // w + 2 <= D - 1 whenever the top chunk is non-zero (the top bit lies below digit D - 1)
+  unsigned long long* p = (((bits >> 63) != 0) != neg ? a.dn : a.dp) + w * T;
+  p[0] += lo & 0xffffffffULL;
+  if (w + 1 < D) p[T] += lo >> 32;
+  if (w + 2 < D) p[2 * T] += hi;
+}
+
+// Row flush, kept out of line: it runs once per row and its many temporaries
+// would otherwise raise the register count of the whole per-entry loop.
+template <int L, int D, int T>
+__device__ __noinline__ void fas_flush(const unsigned long long* dp, const unsigned long long* dn, int base,
+                                       int flags, double* out) {
+  FixAcc<D> r;
+  // each array's digits are below 2^63, so their difference fits a signed digit
+#pragma unroll
+  for (int j = 0; j < D; j++) r.d[j] = (long long)dp[j * T] - (long long)dn[j * T];
+  r.base = base;
+  r.live = flags & 1;
+  r.bad = (flags & 2) != 0;
+  fa_to_mp<L, D>(r, out);
+}
+
+template <int L, int D, int T>
+__device__ __forceinline__ void fas_to_mp(const FixAccS<D, T>& a, double* out) {
+  fas_flush<L, D, T>(a.dp, a.dn, a.base, (a.live ? 1 : 0) | (a.bad ? 2 : 0), out);
+}
+
+}  // namespace mpk

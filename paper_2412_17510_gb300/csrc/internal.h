@@ -47,6 +47,8 @@ struct mpspmv_mat {
   int L, P, Pv;  // components, vector planes, stored value planes
   bool cplx, mixed;
   bool exact = false;  // MPSPMV_EXACT_ACC: products on the binary64 pipe, exact integer accumulation
+  bool dstore = false; // exact arithmetic on binary64 data: only the leading components are stored and
+                       // the products take the MP x binary64 forms (the dropped products are exactly 0)
   unsigned flags;
   int64_t nrows, ncols, nnz, max_row_nnz;
   int32_t K;

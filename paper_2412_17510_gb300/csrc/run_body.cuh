@@ -140,114 +140,127 @@ struct AccDigits {
   static constexpr int D = L == 1 ? 4 : (L == 2 ? 6 : (L == 3 ? 8 : 10));
 };
 
-template <int L, int D>
-__device__ __forceinline__ void add_prod(FixAcc<D>& acc, const mp<L>& a, const mp<L>& x, bool negate) {
-  const double sg = negate ? -1.0 : 1.0;  // exact sign flip of every term
+template <int D, int T>
+__device__ __forceinline__ void acc_add(FixAccS<D, T>& a, double v, bool neg) {
+  fas_add<D, T>(a, v, neg);
+}
+
+template <class Acc, int L>
+__device__ __forceinline__ void add_prod(Acc& acc, const mp<L>& a, const mp<L>& x, bool negate) {
   if constexpr (L == 1) {
     double p, e;
     two_prod(a.v[0], x.v[0], p, e);
-    fa_add<D>(acc, sg * p);
-    fa_add<D>(acc, sg * e);
+    acc_add(acc, p, negate);
+    acc_add(acc, e, negate);
   } else if constexpr (L == 2) {
     double p, e;
     two_prod(a.v[0], x.v[0], p, e);
     const double c = __fma_rn(a.v[0], x.v[1], __dmul_rn(a.v[1], x.v[0]));
-    fa_add<D>(acc, sg * p);
-    fa_add<D>(acc, sg * e);
-    fa_add<D>(acc, sg * c);
+    acc_add(acc, p, negate);
+    acc_add(acc, e, negate);
+    acc_add(acc, c, negate);
   } else if constexpr (L == 3) {
-    double p, e;
-    two_prod(a.v[0], x.v[0], p, e);
-    fa_add<D>(acc, sg * p);
-    fa_add<D>(acc, sg * e);
-    two_prod(a.v[0], x.v[1], p, e);
-    fa_add<D>(acc, sg * p);
-    fa_add<D>(acc, sg * e);
-    two_prod(a.v[1], x.v[0], p, e);
-    fa_add<D>(acc, sg * p);
-    fa_add<D>(acc, sg * e);
+    const int ij[3][2] = {{0, 0}, {0, 1}, {1, 0}};
+#pragma unroll
+    for (int t = 0; t < 3; t++) {
+      double ai = a.v[ij[t][0]], xj = x.v[ij[t][1]], p, e;
+      // keep the products in step with the accumulation (the compiler would
+      // otherwise form every product first and run out of registers)
+      asm volatile("" : "+d"(ai), "+d"(xj)::"memory");
+      two_prod(ai, xj, p, e);
+      acc_add(acc, p, negate);
+      acc_add(acc, e, negate);
+    }
     const double c = __fma_rn(a.v[0], x.v[2], __fma_rn(a.v[1], x.v[1], __dmul_rn(a.v[2], x.v[0])));
-    fa_add<D>(acc, sg * c);
+    acc_add(acc, c, negate);
   } else {
 #pragma unroll
     for (int i = 0; i < 3; i++) {
 #pragma unroll
       for (int j = 0; j < 3 - i; j++) {
-        double p, e;
-        two_prod(a.v[i], x.v[j], p, e);
-        fa_add<D>(acc, sg * p);
-        fa_add<D>(acc, sg * e);
+        double ai = a.v[i], xj = x.v[j], p, e;
+        asm volatile("" : "+d"(ai), "+d"(xj)::"memory");
+        two_prod(ai, xj, p, e);
+        acc_add(acc, p, negate);
+        acc_add(acc, e, negate);
       }
     }
     const double c =
         __fma_rn(a.v[0], x.v[3], __fma_rn(a.v[1], x.v[2], __fma_rn(a.v[2], x.v[1], __dmul_rn(a.v[3], x.v[0]))));
-    fa_add<D>(acc, sg * c);
+    acc_add(acc, c, negate);
   }
 }
 
 // binary64 matrix value (M mode)
-template <int L, int D>
-__device__ __forceinline__ void add_prod_d(FixAcc<D>& acc, double a, const mp<L>& x, bool negate) {
-  const double sg = negate ? -1.0 : 1.0;
+template <class Acc, int L>
+__device__ __forceinline__ void add_prod_d(Acc& acc, double a, const mp<L>& x, bool negate) {
 #pragma unroll
   for (int j = 0; j < L - 1; j++) {
     double p, e;
     two_prod(a, x.v[j], p, e);
-    fa_add<D>(acc, sg * p);
-    fa_add<D>(acc, sg * e);
+    acc_add(acc, p, negate);
+    acc_add(acc, e, negate);
   }
-  fa_add<D>(acc, sg * __dmul_rn(a, x.v[L - 1]));
+  acc_add(acc, __dmul_rn(a, x.v[L - 1]), negate);
 }
 
-template <int L, bool CPLX, bool MIXED, int D>
-__device__ __forceinline__ void accumulate_exact(const DevMat& m, int64_t pos, const double* __restrict__ x,
-                                                 int64_t xs, int64_t xcol_off, FixAcc<D>& sr, FixAcc<D>& si) {
-  const int64_t col = __ldg(m.cols + pos);
-  mp<L> xr, xi;
+// Operands of one stored entry, loaded ahead of their use.
+template <int L, bool CPLX, bool MIXED>
+struct EntryIn {
+  mp<L> xr, xi;  // x[col] (real / imaginary components)
+  mp<L> ar, ai;  // matrix value (MIXED: binary64 in ar.v[0], ai.v[0])
+};
+
+template <int L, bool CPLX, bool MIXED>
+__device__ __forceinline__ void load_entry(const DevMat& m, int64_t pos, int64_t col, const double* __restrict__ x,
+                                           int64_t xs, int64_t xcol_off, EntryIn<L, CPLX, MIXED>& e) {
 #pragma unroll
-  for (int l = 0; l < L; l++) xr.v[l] = __ldg(x + (int64_t)l * xs + col * xcol_off);
+  for (int l = 0; l < L; l++) e.xr.v[l] = __ldg(x + (int64_t)l * xs + col * xcol_off);
   if (CPLX) {
 #pragma unroll
-    for (int l = 0; l < L; l++) xi.v[l] = __ldg(x + (int64_t)(L + l) * xs + col * xcol_off);
+    for (int l = 0; l < L; l++) e.xi.v[l] = __ldg(x + (int64_t)(L + l) * xs + col * xcol_off);
   }
   if (MIXED) {
-    const double ar = __ldg(m.vals + pos);
-    add_prod_d<L, D>(sr, ar, xr, false);
-    if (CPLX) {
-      const double ai = __ldg(m.vals + m.tlen + pos);
-      add_prod_d<L, D>(sr, ai, xi, true);
-      add_prod_d<L, D>(si, ar, xi, false);
-      add_prod_d<L, D>(si, ai, xr, false);
-    }
+    e.ar.v[0] = __ldg(m.vals + pos);
+    if (CPLX) e.ai.v[0] = __ldg(m.vals + m.tlen + pos);
   } else {
-    mp<L> ar;
 #pragma unroll
-    for (int l = 0; l < L; l++) ar.v[l] = __ldg(m.vals + (int64_t)l * m.tlen + pos);
-    add_prod<L, D>(sr, ar, xr, false);
+    for (int l = 0; l < L; l++) e.ar.v[l] = __ldg(m.vals + (int64_t)l * m.tlen + pos);
     if (CPLX) {
-      mp<L> ai;
 #pragma unroll
-      for (int l = 0; l < L; l++) ai.v[l] = __ldg(m.vals + (int64_t)(L + l) * m.tlen + pos);
-      add_prod<L, D>(sr, ai, xi, true);
-      add_prod<L, D>(si, ar, xi, false);
-      add_prod<L, D>(si, ai, xr, false);
+      for (int l = 0; l < L; l++) e.ai.v[l] = __ldg(m.vals + (int64_t)(L + l) * m.tlen + pos);
     }
   }
 }
 
-template <int L, bool CPLX, int D>
-__device__ __forceinline__ void flush_exact(const FixAcc<D>& sr, const FixAcc<D>& si, mp<L>& r, mp<L>& i) {
-  fa_to_mp<L, D>(sr, r.v);
-  if (CPLX) fa_to_mp<L, D>(si, i.v);
+template <int L, bool CPLX, bool MIXED, class Acc>
+__device__ __forceinline__ void compute_entry(const EntryIn<L, CPLX, MIXED>& e, Acc& sr, Acc& si) {
+  if (MIXED) {
+    add_prod_d<Acc, L>(sr, e.ar.v[0], e.xr, false);
+    if (CPLX) {
+      add_prod_d<Acc, L>(sr, e.ai.v[0], e.xi, true);
+      add_prod_d<Acc, L>(si, e.ar.v[0], e.xi, false);
+      add_prod_d<Acc, L>(si, e.ai.v[0], e.xr, false);
+    }
+  } else {
+    add_prod<Acc, L>(sr, e.ar, e.xr, false);
+    if (CPLX) {
+      add_prod<Acc, L>(sr, e.ai, e.xi, true);
+      add_prod<Acc, L>(si, e.ar, e.xi, false);
+      add_prod<Acc, L>(si, e.ai, e.xr, false);
+    }
+  }
 }
 
-// Same run structure, carries and empty-row handling as process_run.
-template <int L, bool CPLX, bool MIXED>
+// Same run structure, carries and empty-row handling as process_run.  T is
+// the block size (the accumulator digits of the block live in shared memory).
+template <int L, bool CPLX, bool MIXED, int T>
 __device__ __forceinline__ void process_run_exact(const DevMat& m, int64_t c, int rhs, const double* __restrict__ x,
                                                   int64_t xs, int64_t xoff, double* __restrict__ y, int64_t ys,
                                                   int64_t yoff, double* __restrict__ carry, int kc) {
   constexpr int P = CPLX ? 2 * L : L;
   constexpr int D = AccDigits<L>::D;
+  __shared__ unsigned long long s_digits[(CPLX ? 4 : 2) * D * T];
   const double* xr = x + rhs;
   double* yr = y + rhs;
   const int64_t k0 = c * m.K;
@@ -260,19 +273,36 @@ __device__ __forceinline__ void process_run_exact(const DevMat& m, int64_t c, in
   if (c == 0) {
     for (int64_t r = 0; r < row; r++) store_mp<L, CPLX>(yr, ys, r * yoff, z, z);
   }
-  FixAcc<D> sr, si;
-  fa_reset<D>(sr);
-  fa_reset<D>(si);
+  FixAccS<D, T> sr, si;
+  sr.dp = s_digits + threadIdx.x;
+  sr.dn = s_digits + D * T + threadIdx.x;
+  si.dp = s_digits + (CPLX ? 2 * D * T : 0) + threadIdx.x;
+  si.dn = s_digits + (CPLX ? 3 * D * T : D * T) + threadIdx.x;
+  fas_reset<D, T>(sr);
+  if (CPLX) fas_reset<D, T>(si);
   bool have = false;
   const int n = (int)(k1 - k0);
   const int64_t chunk_base = tile_pos(c, 0, m.K);
+  // software pipeline: column indices two entries ahead, values and x one
+  // entry ahead, so the gathers overlap the integer work of the current entry
+  EntryIn<L, CPLX, MIXED> cur, nxt;
+  int64_t col1 = 0;
+  if (n > 0) load_entry<L, CPLX, MIXED>(m, chunk_base, __ldg(m.cols + chunk_base), xr, xs, xoff, cur);
+  if (n > 1) col1 = __ldg(m.cols + chunk_base + 32);
+#pragma unroll 1
   for (int j = 0; j < n; j++) {
-    accumulate_exact<L, CPLX, MIXED, D>(m, chunk_base + (int64_t)j * 32, xr, xs, xoff, sr, si);
+    int64_t col2 = 0;
+    if (j + 1 < n) load_entry<L, CPLX, MIXED>(m, chunk_base + (int64_t)(j + 1) * 32, col1, xr, xs, xoff, nxt);
+    if (j + 2 < n) col2 = __ldg(m.cols + chunk_base + (int64_t)(j + 2) * 32);
+    compute_entry<L, CPLX, MIXED>(cur, sr, si);
+    cur = nxt;
+    col1 = col2;
     have = true;
     const int64_t kk = k0 + j + 1;
     if (kk == rend) {
-      mp<L> vr, vi;
-      flush_exact<L, CPLX, D>(sr, si, vr, vi);
+      mp<L> vr, vi = z;
+      fas_to_mp<L, D, T>(sr, vr.v);
+      if (CPLX) fas_to_mp<L, D, T>(si, vi.v);
       if (row == first_row && first_partial) {
 #pragma unroll
         for (int p = 0; p < P; p++)
@@ -280,8 +310,8 @@ __device__ __forceinline__ void process_run_exact(const DevMat& m, int64_t c, in
       } else {
         store_mp<L, CPLX>(yr, ys, row * yoff, vr, vi);
       }
-      fa_reset<D>(sr);
-      fa_reset<D>(si);
+      fas_reset<D, T>(sr);
+      if (CPLX) fas_reset<D, T>(si);
       have = false;
       row++;
       while (row < m.nrows && __ldg(m.indptr + row + 1) == kk) {
@@ -292,8 +322,9 @@ __device__ __forceinline__ void process_run_exact(const DevMat& m, int64_t c, in
     }
   }
   if (have) {
-    mp<L> vr, vi;
-    flush_exact<L, CPLX, D>(sr, si, vr, vi);
+    mp<L> vr, vi = z;
+    fas_to_mp<L, D, T>(sr, vr.v);
+    if (CPLX) fas_to_mp<L, D, T>(si, vi.v);
     const int w = (row == first_row && first_partial) ? 0 : 1;
 #pragma unroll
     for (int p = 0; p < P; p++)

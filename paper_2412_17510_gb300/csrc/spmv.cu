@@ -73,7 +73,7 @@ __global__ void build_tiles_kernel(DevMat m, int32_t* __restrict__ cols_out, dou
 // partial, w = 1 last-row partial.
 // ---------------------------------------------------------------------------
 template <int L, bool CPLX, bool MIXED, bool EXACT>
-__global__ void __launch_bounds__(kThreads) spmv_runs_kernel(DevMat m, const double* __restrict__ x, int64_t xs,
+__global__ void __launch_bounds__(kThreads, EXACT ? 3 : 1) spmv_runs_kernel(DevMat m, const double* __restrict__ x, int64_t xs,
                                                              int64_t xoff, double* __restrict__ y, int64_t ys,
                                                              int64_t yoff, double* __restrict__ carry, int kc,
                                                              int kp, int k, const int* __restrict__ gate) {
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) spmv_runs_kernel(DevMat m, const dou
   const int64_t c = t / kp;
   const int rhs = (int)(t - c * kp);
   if (c >= m.nchunks || rhs >= k) return;
-  if (EXACT) process_run_exact<L, CPLX, MIXED>(m, c, rhs, x, xs, xoff, y, ys, yoff, carry, kc);
+  if (EXACT) process_run_exact<L, CPLX, MIXED, kThreads>(m, c, rhs, x, xs, xoff, y, ys, yoff, carry, kc);
   else process_run<L, CPLX, MIXED>(m, c, rhs, x, xs, xoff, y, ys, yoff, carry, kc);
 }
 
@@ -259,7 +259,7 @@ int build_one(mpspmv_mat* h, const double* vin, int64_t nin, int vin_limbs, cons
 // Precision / complex / mode dispatch.
 #define MPS_DISPATCH(FN, h, ...)                                                   \
   do {                                                                            \
-    switch ((h)->L * 4 + ((h)->cplx ? 2 : 0) + ((h)->mixed ? 1 : 0)) {            \
+    switch ((h)->L * 4 + ((h)->cplx ? 2 : 0) + (((h)->mixed || (h)->dstore) ? 1 : 0)) { \
       case 1 * 4 + 0: return FN<1, false, false>(__VA_ARGS__);                    \
       case 1 * 4 + 2: return FN<1, true, false>(__VA_ARGS__);                     \
       case 2 * 4 + 0: return FN<2, false, false>(__VA_ARGS__);                    \

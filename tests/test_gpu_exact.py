@@ -141,3 +141,29 @@ def test_stencil_full_size_sampled_rows():
                 assert exact.bound_ratio(y[:, rows], A, x, rows=rows) <= 1.0
             finally:
                 mps.mpspmv_destroy(h)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_binary64_storage_is_bit_identical(L, cplx):
+    """Exact accumulation on binary64 data stores the leading components only
+    and uses the MP x binary64 product forms; the products it leaves out are
+    exactly zero, so the result equals that of the full P-mode storage (the
+    same values passed with explicit zero lower components) bit for bit."""
+    coo = workloads.random_sparse(700, 650, 40, seed=30 + L, cplx=cplx, empty_frac=0.1)
+    fl = EX | (1 if cplx else 0)
+    h1 = mps.mpspmv_create_csr(700, 650, coo.row, coo.col, coo.val, L, fl, val_limbs=1)
+    h2 = mps.mpspmv_create_csr(700, 650, coo.row, coo.col, coo.promoted(L), L, fl, val_limbs=L)
+    try:
+        assert mps.mpspmv_get_info(h1)["value_planes"] == (2 if cplx else 1)
+        assert mps.mpspmv_get_info(h2)["value_planes"] == (2 * L if cplx else L)
+        P = 2 * L if cplx else L
+        x = workloads.full_limb_vector(650, L, seed=8, cplx=cplx)
+        y1 = gpu_spmv(h1, x, P, 700)
+        y2 = gpu_spmv(h2, x, P, 700)
+        assert np.array_equal(y1, y2)
+        A = oracle.coo_to_csr(700, 650, coo.row, coo.col, coo.promoted(L), L, cplx)
+        assert exact.bound_ratio(y1, A, x) <= 1.0
+    finally:
+        mps.mpspmv_destroy(h1)
+        mps.mpspmv_destroy(h2)

@@ -121,7 +121,7 @@ class ClockSampler:
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("spmv.cu", "mp_arith.cuh", "run_body.cuh", "fixacc.cuh"):
+    for f in ("spmv.cu", "mp_arith.cuh", "run_body.cuh", "fixacc.cuh", "exact_prod.cuh"):
         with open(os.path.join(ROOT, "paper_2412_17510_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -266,30 +266,74 @@ def suite_complex(mps, fp64_fma, hbm, stream, small):
     coo = workloads.complex_sym_banded(n, 48, 0.3, seed=0)
     out = {"workload": "complex-symmetric band n=%d hbw=48 fill 0.3 (nnz=%d complex)" % (n, coo.nnz)}
     for L in (2, 4):
-        h = mps.mpspmv_create_csr(n, n, coo.row, coo.col, coo.val, L, mps.MPSPMV_COMPLEX, val_limbs=1)
-        x = torch.from_numpy(workloads.full_limb_vector(n, L, seed=0, cplx=True)).cuda()
-        y = torch.empty_like(x)
-        for _ in range(3):
-            mps.mpspmv_spmv(h, x, y, stream)
-        ms = _time_events(lambda: mps.mpspmv_spmv(h, x, y, stream), 10, stream)
-        ops = coo.nnz * 4 * OPS_PER_ENTRY[L]
-        byts = coo.nnz * (4 + 16 * L) + n * (8 + 16 * L) + n * 16 * L
-        troof = max(ops / fp64_fma, byts / (hbm * 1e9))
-        out["spmv_%s" % PNAME[L]] = {"ms": ms, "gnnz_s": coo.nnz / ms / 1e6, "roofline_frac": troof / (ms * 1e-3)}
-        mps.mpspmv_destroy(h)
+        for sfx, fl in (("", 0), ("_exact", 16)):
+            h = mps.mpspmv_create_csr(n, n, coo.row, coo.col, coo.val, L, mps.MPSPMV_COMPLEX | fl, val_limbs=1)
+            vp = mps.mpspmv_get_info(h)["value_planes"]
+            x = torch.from_numpy(workloads.full_limb_vector(n, L, seed=0, cplx=True)).cuda()
+            y = torch.empty_like(x)
+            for _ in range(3):
+                mps.mpspmv_spmv(h, x, y, stream)
+            ms = _time_events(lambda: mps.mpspmv_spmv(h, x, y, stream), 10, stream)
+            if fl:
+                per = OPS_PER_ENTRY_EXACT_D[L] if vp == 2 else OPS_PER_ENTRY_EXACT[L]
+            else:
+                per = OPS_PER_ENTRY[L]
+            ops = coo.nnz * 4 * per
+            byts = coo.nnz * (4 + 8 * vp) + n * (8 + 16 * L) + n * 16 * L
+            troof = max(ops / fp64_fma, byts / (hbm * 1e9))
+            out["spmv_%s%s" % (PNAME[L], sfx)] = {"ms": ms, "gnnz_s": coo.nnz / ms / 1e6,
+                                                  "roofline_frac": troof / (ms * 1e-3)}
+            mps.mpspmv_destroy(h)
     shifted = workloads.complex_sym_banded(n, 48, 0.3, seed=0, shift=50 + 10j)
     for L in (2, 4):
-        h = mps.mpspmv_create_csr(n, n, shifted.row, shifted.col, shifted.val, L, mps.MPSPMV_COMPLEX, val_limbs=1)
-        xt = torch.from_numpy(workloads.full_limb_vector(n, L, seed=1, cplx=True)).cuda()
-        b = torch.empty_like(xt)
-        mps.mpspmv_spmv(h, xt, b, stream)
-        x = torch.zeros_like(b)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, it, rr = mps.mpspmv_bicgstab(h, b, x, 1e-28, 0.0, 5000, stream)
-        torch.cuda.synchronize()
-        out["bicgstab_%s" % PNAME[L]] = {"status": st, "iters": it, "relres": rr, "s": time.perf_counter() - t0}
-        mps.mpspmv_destroy(h)
+        for sfx, fl in (("", 0), ("_exact", 16)):
+            h = mps.mpspmv_create_csr(n, n, shifted.row, shifted.col, shifted.val, L, mps.MPSPMV_COMPLEX | fl,
+                                      val_limbs=1)
+            xt = torch.from_numpy(workloads.full_limb_vector(n, L, seed=1, cplx=True)).cuda()
+            b = torch.empty_like(xt)
+            mps.mpspmv_spmv(h, xt, b, stream)
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, it, rr = mps.mpspmv_bicgstab(h, b, x, 1e-28, 0.0, 5000, stream)
+            torch.cuda.synchronize()
+            out["bicgstab_%s%s" % (PNAME[L], sfx)] = {"status": st, "iters": it, "relres": rr,
+                                                      "s": time.perf_counter() - t0}
+            mps.mpspmv_destroy(h)
+    return out
+
+
+def suite_cg(mps, stream, small):
+    """CG on the SPD 7-point diffusion matrix on a 128^3 grid (kappa
+    log-uniform in [0.1, 10]), a fixed 200 iterations (rtol = 0), paper-order
+    and exact-accumulation handles: ms per iteration, and the SpMV's ms for
+    comparison (the rest is the vector kernels and the scalar steps)."""
+    import torch
+    N = 48 if small else 128
+    coo = workloads.diffusion_7pt(N, N, N, kappa_range=(0.1, 10.0), seed=0)
+    n = coo.nrows
+    out = {"workload": "7-point diffusion %d^3 (n=%d, nnz=%d), 200 CG iterations" % (N, n, coo.nnz)}
+    its = 200
+    for L in (2, 3, 4):
+        for arith, fl in (("paper", 0), ("exact", 16)):
+            h = mps.mpspmv_create_csr(n, n, coo.row, coo.col, coo.val, L, fl, val_limbs=1)
+            b = torch.from_numpy(workloads.full_limb_vector(n, L, seed=1)).cuda()
+            x = torch.zeros_like(b)
+            y = torch.empty_like(b)
+            mps.mpspmv_cg(h, b, x, 0.0, 0.0, 8, stream)  # workspace, graph warm-up
+            for _ in range(3):
+                mps.mpspmv_spmv(h, b, y, stream)
+            spmv_ms = _time_events(lambda: mps.mpspmv_spmv(h, b, y, stream), 10, stream)
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, it, rr = mps.mpspmv_cg(h, b, x, 0.0, 0.0, its, stream)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3 / max(it, 1)
+            out["cg_%s_%s" % (PNAME[L], arith)] = {"ms_per_iter": ms, "spmv_ms": spmv_ms, "iters": it,
+                                                   "relres": rr, "status": st}
+            mps.mpspmv_destroy(h)
+            del b, x, y
     return out
 
 
@@ -400,8 +444,9 @@ def main():
                     help="paper: the paper's DD/TD/QD operation sequences; exact: error-free products on the "
                          "binary64 pipe with exact integer accumulation (MPSPMV_EXACT_ACC); both: value from "
                          "exact, the paper-order step timed too")
-    ap.add_argument("--suite", action="store_true",
-                    help="also measure the complex, batched and selector workloads (adds minutes)")
+    ap.add_argument("--suite", nargs="?", const="complex,cg,batched,selector", default=None,
+                    help="also measure the complex, CG, batched and selector workloads (adds minutes); "
+                         "optionally a comma-separated subset")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -597,9 +642,15 @@ def main():
     suite = None
     if args.suite and rank == 0:
         del flush
-        suite = {"complex": suite_complex(mps, fp64_fma, hbm, stream, args.small),
-                 "batched": suite_batched(mps, stream, args.small),
-                 "selector": suite_selector(mps, args.small)}
+        parts = {"complex": lambda: suite_complex(mps, fp64_fma, hbm, stream, args.small),
+                 "cg": lambda: suite_cg(mps, stream, args.small),
+                 "batched": lambda: suite_batched(mps, stream, args.small),
+                 "selector": lambda: suite_selector(mps, args.small)}
+        suite = {}
+        for name in args.suite.split(","):
+            if name not in parts:
+                raise SystemExit("unknown suite part %r" % name)
+            suite[name] = parts[name]()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

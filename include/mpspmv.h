@@ -179,6 +179,35 @@ int mpspmv_bicgstab(mpspmv_h h, const double* b, double* x, double rtol, double 
                     double* relres, void* stream);
 
 /*
+ * Krylov vector operations in the handle's precision and arithmetic (the
+ * inner products and vector updates of Section 4.2's CG and BiCGSTAB, with
+ * every vector and scalar in DD / TD / QD).  The handle supplies L, real or
+ * complex, and the arithmetic only; n is the vectors' own length (plane
+ * stride), n >= 0.  Vectors are device arrays of P planes of n (complex: the
+ * L real planes, then the L imaginary planes).
+ *   Paper order (default): each product and sum in the MP arithmetic of
+ *     Algorithms 1-5; mpspmv_axpy is bit-identical, element by element, to
+ *     the same operations done in sequence.
+ *   MPSPMV_EXACT_ACC handles: each updated element is formed from the
+ *     error-free products in one exact fixed-point sum and rounded (truncated)
+ *     to L components once; each thread's share of an inner product is summed
+ *     exactly, the shares are added in MP arithmetic.  mpspmv_cg and
+ *     mpspmv_bicgstab use the same kernels for such handles.
+ *
+ * mpspmv_dot -- out (host, 2L doubles) = sum_i conj(u_i) v_i: out[0..L) the
+ *   real part's components, out[L..2L) the imaginary part's (zeros for a real
+ *   handle).  Synchronises `stream`.
+ * mpspmv_axpy -- w = u + alpha v; alpha (host, 2L doubles, same layout as
+ *   out; the imaginary part is ignored for a real handle).  w may be u or v
+ *   (element-wise in place); other overlaps are undefined.  Asynchronous.
+ * Both return MPSPMV_EINVAL for a NULL handle, n < 0, or a NULL vector or
+ * scalar with n > 0 (mpspmv_dot: a NULL out always).
+ */
+int mpspmv_dot(mpspmv_h h, int64_t n, const double* u, const double* v, double* out, void* stream);
+int mpspmv_axpy(mpspmv_h h, int64_t n, const double* alpha, const double* u, const double* v, double* w,
+                void* stream);
+
+/*
  * Batched products and solves over many independent matrices of one
  * precision (real, P mode, nnz > 0 each), each with k_i right-hand sides
  * (1 <= k_i <= 32).  The paper multiplies one matrix at a time (Sections 3

@@ -64,6 +64,8 @@ def _load():
                       ctypes.POINTER(ctypes.c_double), vp],
         "mpspmv_bicgstab": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
                             ctypes.POINTER(ctypes.c_double), vp],
+        "mpspmv_dot": [vp, i64, vp, vp, vp, vp],
+        "mpspmv_axpy": [vp, i64, vp, vp, vp, vp, vp],
         "mpspmv_spmv_csr_noalloc": [c_int, ctypes.c_uint, i64, i64, i64, vp, vp, vp, vp, vp, vp],
         "mpspmv_batch_create": [vp, vp, c_int, ctypes.c_uint, ctypes.POINTER(vp), vp],
         "mpspmv_batch_destroy": [vp],
@@ -186,6 +188,28 @@ def mpspmv_cg(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=
 def mpspmv_bicgstab(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=False):
     """BiCGSTAB in place on x.  Returns (status, iterations, true relative residual)."""
     return _solve(_lib.mpspmv_bicgstab, "mpspmv_bicgstab", h, b, x, rtol, atol, maxit, stream, raise_on_noconv)
+
+
+def mpspmv_dot(h, n, u, v, stream=None):
+    """sum_i conj(u_i) v_i of device vectors (P planes of n) in the handle's
+    precision and arithmetic; returns (re, im) as two arrays of L components."""
+    L = mpspmv_get_info(h)["prec"]
+    out = np.zeros(2 * L)
+    _check(_lib.mpspmv_dot(h, n, _ptr(u), _ptr(v), out.ctypes.data, _stream(stream)), "mpspmv_dot")
+    return out[:L].copy(), out[L:].copy()
+
+
+def mpspmv_axpy(h, n, alpha_re, u, v, w, alpha_im=None, stream=None):
+    """w = u + alpha v on device vectors; alpha_re / alpha_im are scalars or
+    arrays of up to L components."""
+    L = mpspmv_get_info(h)["prec"]
+    a = np.zeros(2 * L)
+    ar = np.atleast_1d(np.asarray(alpha_re, dtype=np.float64))
+    a[:ar.size] = ar
+    if alpha_im is not None:
+        ai = np.atleast_1d(np.asarray(alpha_im, dtype=np.float64))
+        a[L:L + ai.size] = ai
+    _check(_lib.mpspmv_axpy(h, n, a.ctypes.data, _ptr(u), _ptr(v), _ptr(w), _stream(stream)), "mpspmv_axpy")
 
 
 def mpspmv_spmv_csr_noalloc(prec, flags, nrows, ncols, nnz, indptr, indices, vals, x, y, stream=None):

@@ -8,7 +8,7 @@ struct KrylovState {
   int status;
   int iter;
   int maxit;
-  int pad;
+  int exact;      // 1: inner products summed exactly (MPSPMV_EXACT_ACC handles)
   double tol;     // rtol * ||b|| + atol
   double bnorm;   // ||b||_2 (binary64)
   double relres;  // ||b - A x|| / ||b|| at exit

@@ -52,3 +52,11 @@ def test_host_side_validation_without_device():
         with pytest.raises(mps.MpspmvError) as e:
             mps.mpspmv_create_csr(**c)
         assert e.value.status == mps.MPSPMV_EINVAL, c
+
+
+def test_vector_ops_reject_null_handle_on_host():
+    import paper_2412_17510_gb300 as mps
+    lib = mps.library()
+    out = np.zeros(8)
+    assert lib.mpspmv_dot(None, 4, None, None, out.ctypes.data, None) == mps.MPSPMV_EINVAL
+    assert lib.mpspmv_axpy(None, 4, out.ctypes.data, None, None, None, None) == mps.MPSPMV_EINVAL

@@ -115,6 +115,24 @@ __device__ __forceinline__ unsigned long long fa_bits(const unsigned int (&dig)[
   return r;
 }
 
+// chunk * 2^e with the sign neg, exact for 0 <= chunk < 2^53.  A normal
+// result is assembled from its fields on the integer pipe (sign, biased
+// exponent of the top bit, the 52 bits below it); the rest goes through
+// scalbn.  GB300 runs conversions and binary64 scaling on the slow binary64
+// pipe, which the per-row flush would otherwise occupy.
+__device__ __forceinline__ double chunk_to_double(unsigned long long chunk, int e, bool neg) {
+  if (chunk == 0) return neg ? -0.0 : 0.0;
+  const int k = 63 - __clzll((long long)chunk);  // top bit, 0 .. 52
+  const int E = k + e;                           // chunk * 2^e lies in [2^E, 2^(E+1))
+  if (E >= -1022 && E <= 1023) {
+    const unsigned long long frac = (chunk << (52 - k)) & ((1ULL << 52) - 1);
+    return __longlong_as_double((long long)(((neg ? 1ULL : 0ULL) << 63) |
+                                            ((unsigned long long)(E + 1023) << 52) | frac));
+  }
+  const double c = scalbn((double)chunk, e);
+  return neg ? -c : c;
+}
+
 // Cut the accumulated value into L binary64 components (truncation).
 template <int L, int D>
 __device__ __forceinline__ void fa_to_mp(const FixAcc<D>& a, double* out) {
@@ -163,8 +181,7 @@ __device__ __forceinline__ void fa_to_mp(const FixAcc<D>& a, double* out) {
     } else {
       chunk = (fa_bits<D>(dig, 0) << (-lsb)) & ((1ULL << 53) - 1);
     }
-    const double c = scalbn((double)chunk, lsb + a.base);  // exact: chunk < 2^53
-    out[l] = neg ? -c : c;
+    out[l] = chunk_to_double(chunk, lsb + a.base, neg);  // exact: chunk < 2^53
   }
 }
 

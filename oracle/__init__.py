@@ -57,6 +57,8 @@ def _load(counting=False):
         "oracle_mp_div": (None, [c_int, _dp, _dp, _dp]),
         "oracle_coo_to_csr": (c_i64, [c_i64, c_i64, c_i64, _i64p, _i64p, _dp, c_int, c_int, _i64p, _i32p, _dp]),
         "oracle_spmv": (None, [c_int, c_int, c_int, c_i64, _i64p, _i32p, _dp, c_i64, _dp, c_i64, _dp, c_i64]),
+        "oracle_spmtv": (None, [c_int, c_int, c_int, c_i64, c_i64, _i64p, _i32p, _dp, c_i64, _dp, c_i64, _dp,
+                                c_i64]),
         "oracle_spmv_rows": (None, [c_int, c_int, c_int, c_i64, _i64p, _i64p, _i32p, _dp, c_i64, _dp, c_i64, _dp]),
         "oracle_spmm": (None, [c_int, c_int, c_i64, c_i64, _i64p, _i32p, _dp, c_i64, c_int, _dp, c_i64, c_i64,
                                _dp, c_i64, c_i64]),
@@ -231,6 +233,17 @@ def spmv(A, x, mixed=False, counting=False):
     y = np.zeros((A.P, A.nrows))
     lib.oracle_spmv(A.L, int(A.cplx), int(mixed), A.nrows, A.indptr.ctypes.data_as(_i64p),
                     A.indices.ctypes.data_as(_i32p), _d(A.data), A.data.shape[1], _d(x), x.shape[1], _d(y), A.nrows)
+    return y
+
+
+def spmtv(A, x, mixed=False):
+    """y = A^T x (transpose, no conjugation) in the working precision, by the
+    row-oriented scatter; x has shape (P, nrows), y (P, ncols)."""
+    x = _f64(x)
+    y = np.zeros((A.P, A.ncols))
+    _load().oracle_spmtv(A.L, int(A.cplx), int(mixed), A.nrows, A.ncols, A.indptr.ctypes.data_as(_i64p),
+                         A.indices.ctypes.data_as(_i32p), _d(A.data), A.data.shape[1], _d(x), x.shape[1], _d(y),
+                         A.ncols)
     return y
 
 

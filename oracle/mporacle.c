@@ -515,6 +515,61 @@ void oracle_spmv(int L, int cplx, int mixed, int64_t nrows, const int64_t* indpt
   }
 }
 
+/* SpTMV y = A^T x (Section 4, "A^T v"; complex: transpose, no conjugation),
+ * in the row-oriented scatter form: rows i in increasing order, and each
+ * stored entry a_ik of row i adds a_ik x_i into y_k.  Every y_k therefore
+ * sums its products in increasing i, starting from zero.  x: P planes of
+ * nrows (stride xs); y: P planes of ncols (stride ys), overwritten.  The
+ * products and signs of one entry follow spmv_row. */
+void oracle_spmtv(int L, int cplx, int mixed, int64_t nrows, int64_t ncols, const int64_t* indptr,
+                  const int32_t* indices, const double* data, int64_t dstride, const double* x, int64_t xs,
+                  double* y, int64_t ys) {
+  int P = cplx ? 2 * L : L;
+  for (int p = 0; p < P; p++)
+    for (int64_t j = 0; j < ncols; j++) y[(int64_t)p * ys + j] = 0.0;
+  for (int64_t i = 0; i < nrows; i++) {
+    double xr[4], xi[4], a[4], ai[4], t[4], yr[4], yi[4];
+    for (int l = 0; l < L; l++) xr[l] = x[(int64_t)l * xs + i];
+    if (cplx) for (int l = 0; l < L; l++) xi[l] = x[(int64_t)(L + l) * xs + i];
+    for (int64_t k = indptr[i]; k < indptr[i + 1]; k++) {
+      int64_t j = indices[k];
+      for (int l = 0; l < L; l++) yr[l] = y[(int64_t)l * ys + j];
+      if (cplx) for (int l = 0; l < L; l++) yi[l] = y[(int64_t)(L + l) * ys + j];
+      if (mixed) {
+        double ad = data[k];
+        mp_mul_d(L, xr, ad, t);
+        mp_add(L, yr, t, yr);
+        if (cplx) {
+          double aid = data[dstride + k];
+          mp_mul_d(L, xi, aid, t);
+          mp_neg(L, t, t);
+          mp_add(L, yr, t, yr);
+          mp_mul_d(L, xi, ad, t);
+          mp_add(L, yi, t, yi);
+          mp_mul_d(L, xr, aid, t);
+          mp_add(L, yi, t, yi);
+        }
+      } else {
+        for (int l = 0; l < L; l++) a[l] = data[(int64_t)l * dstride + k];
+        mp_mul(L, a, xr, t);
+        mp_add(L, yr, t, yr);
+        if (cplx) {
+          for (int l = 0; l < L; l++) ai[l] = data[(int64_t)(L + l) * dstride + k];
+          mp_mul(L, ai, xi, t);
+          mp_neg(L, t, t);
+          mp_add(L, yr, t, yr);
+          mp_mul(L, a, xi, t);
+          mp_add(L, yi, t, yi);
+          mp_mul(L, ai, xr, t);
+          mp_add(L, yi, t, yi);
+        }
+      }
+      for (int l = 0; l < L; l++) y[(int64_t)l * ys + j] = yr[l];
+      if (cplx) for (int l = 0; l < L; l++) y[(int64_t)(L + l) * ys + j] = yi[l];
+    }
+  }
+}
+
 /* Selected rows only: y is P planes of nsel (row rows[s] goes to column s). */
 void oracle_spmv_rows(int L, int cplx, int mixed, int64_t nsel, const int64_t* rows, const int64_t* indptr,
                       const int32_t* indices, const double* data, int64_t dstride, const double* x, int64_t xs,

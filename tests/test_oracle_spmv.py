@@ -231,3 +231,55 @@ def test_exact_module_pins():
     cr, ci = exact.sqrt_2p3i_fixed()
     zr, zi = F(cr, 1 << 1200), F(ci, 1 << 1200)
     assert abs(zr * zr - zi * zi - 2) < F(1, 2 ** 1180) and abs(2 * zr * zi - 3) < F(1, 2 ** 1180)
+
+
+# ---------------------------------------------------------------------------
+# SpTMV y = A^T x (Section 4, "A^T v"): the oracle's row-oriented scatter
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_spmtv_worked_example_brute_force(L):
+    g = worked()
+    v = np.zeros((L, 8)); v[0] = g["coo"]["data"]
+    A = oracle.coo_to_csr(5, 5, g["coo"]["row"], g["coo"]["col"], v, L)
+    x = np.zeros((L, 5)); x[0] = [1, 2, 3, 4, 5]
+    y = oracle.spmtv(A, x)
+    ref = [sum(d * (r + 1) for d, r, c in zip(g["coo"]["data"], g["coo"]["row"], g["coo"]["col"]) if c == j)
+           for j in range(5)]
+    assert y[0].tolist() == ref
+    assert not y[1:].any()
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_spmtv_equals_spmv_of_the_transpose(L, cplx):
+    """The scatter sums each y_j in increasing row order, the order of row j
+    of the transposed CSR: bit-identical to the row sum of A^T built from the
+    swapped triplets, and within the exact bound."""
+    coo = workloads.random_sparse(70, 50, 8, seed=20 + L, cplx=cplx, L=L, full_limb=True, empty_frac=0.1)
+    A = oracle.coo_to_csr(70, 50, coo.row, coo.col, coo.val, L, cplx)
+    AT = oracle.coo_to_csr(50, 70, coo.col, coo.row, coo.val, L, cplx)
+    x = workloads.full_limb_vector(70, L, seed=5, cplx=cplx)
+    y = oracle.spmtv(A, x)
+    assert y.shape == (A.P, 50)
+    assert np.array_equal(y, oracle.spmv(AT, x))
+    assert exact.bound_ratio(y, AT, x) <= 1.0
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_spmtv_mixed_mode_and_duplicates(L):
+    coo = workloads.random_sparse(40, 30, 10, seed=9)
+    A1 = oracle.coo_to_csr(40, 30, coo.row, coo.col, coo.val, 1)
+    AT1 = oracle.coo_to_csr(30, 40, coo.col, coo.row, coo.val, 1)
+    Am = oracle.CSR(40, 30, A1.indptr, A1.indices, A1.data, L, False)
+    ATm = oracle.CSR(30, 40, AT1.indptr, AT1.indices, AT1.data, L, False)
+    x = workloads.full_limb_vector(40, L, seed=6)
+    assert np.array_equal(oracle.spmtv(Am, x, mixed=True), oracle.spmv(ATm, x, mixed=True))
+    # integer data with duplicated triplets: exact
+    ic = workloads.integer_matrix(30, 25, 0.2, seed=3, dup_frac=0.3)
+    Ai = oracle.coo_to_csr(30, 25, ic.row, ic.col, ic.promoted(L), L)
+    xi = workloads.integer_vector(30, L, seed=2)
+    dense = np.zeros((30, 25))
+    np.add.at(dense, (ic.row, ic.col), ic.val[0])
+    ref = dense.T @ xi[0]
+    yi = oracle.spmtv(Ai, xi)
+    assert np.array_equal(yi[0], ref) and not yi[1:].any()

@@ -60,6 +60,8 @@ typedef enum { MPSPMV_D = 1, MPSPMV_DD = 2, MPSPMV_TD = 3, MPSPMV_QD = 4 } mpspm
                                 exactly in fixed point on the integer pipe, then cut to L components.
                                 Same bound 8 m u (|A||x|)_i (usually far smaller error); results are not
                                 bit-identical to the paper-order arithmetic. */
+#define MPSPMV_TRANSPOSE 32u /* also build A^T (a second internal matrix from the swapped triplets, about
+                                doubling the device bytes) for mpspmv_spmtv and mpspmv_bicg */
 
 typedef struct mpspmv_mat* mpspmv_h;
 
@@ -97,7 +99,8 @@ typedef struct {
  *             NaN or Inf -> MPSPMV_EINVAL.
  *  val_limbs  1..prec (exactly 1 with MPSPMV_MIXED).
  *  prec       MPSPMV_DD, MPSPMV_TD or MPSPMV_QD (MPSPMV_D: binary64).
- *  flags      MPSPMV_COMPLEX | MPSPMV_MIXED | MPSPMV_SYMMETRIC | MPSPMV_ONE_BASED.
+ *  flags      MPSPMV_COMPLEX | MPSPMV_MIXED | MPSPMV_SYMMETRIC | MPSPMV_ONE_BASED |
+ *             MPSPMV_EXACT_ACC | MPSPMV_TRANSPOSE.
  *  stream     stream for the uploads and the device-side build.
  *
  * Triplets are ordered by (row, col); duplicates are summed in the working
@@ -130,6 +133,23 @@ int mpspmv_get_info(mpspmv_h h, mpspmv_info* info);
  * the longest row and u = 2^-104, 2^-155, 2^-207 (DD, TD, QD).  Asynchronous.
  */
 int mpspmv_spmv(mpspmv_h h, const double* x, double* y, void* stream);
+
+/*
+ * mpspmv_spmtv -- y = A^T x (Section 4, "SpTMV"; complex: the transpose, not
+ * the conjugate transpose).  Requires a handle created with MPSPMV_TRANSPOSE
+ * (MPSPMV_ENOTSUP otherwise).
+ *
+ *  x  device, P planes of nrows (read only).
+ *  y  device, P planes of ncols (overwritten; must not overlap x).
+ *
+ * A^T is stored as its own matrix, built once at creation from the swapped
+ * triplets, so the product is a row sum like mpspmv_spmv and needs no
+ * scatter or combining step.  Each y_j adds its products in increasing row
+ * of A, the order of the row-oriented scatter (rows of A in order, each
+ * entry a_ij adding a_ij x_i into y_j).  Same bound as mpspmv_spmv with m
+ * the longest column of A.  Asynchronous.
+ */
+int mpspmv_spmtv(mpspmv_h h, const double* x, double* y, void* stream);
 
 /*
  * mpspmv_spmv_host -- mpspmv_spmv with host buffers: copies x (P planes of

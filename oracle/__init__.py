@@ -65,7 +65,13 @@ def _load(counting=False):
         "oracle_cg": (c_int, [c_int, c_i64, _i64p, _i32p, _dp, c_i64, _dp, _dp, c_dbl, c_dbl, c_int,
                               ctypes.POINTER(c_int), _dp]),
         "oracle_bicgstab": (c_int, [c_int, c_int, c_i64, _i64p, _i32p, _dp, c_i64, _dp, _dp, c_dbl, c_dbl, c_int,
-                                    ctypes.POINTER(c_int), _dp]),
+                                ctypes.POINTER(c_int), _dp]),
+        "oracle_bicg": (c_int, [c_int, c_int, c_i64, _i64p, _i32p, _dp, c_i64, _dp, _dp, c_dbl, c_dbl, c_int,
+                                ctypes.POINTER(c_int), _dp]),
+        "oracle_cgs": (c_int, [c_int, c_int, c_i64, _i64p, _i32p, _dp, c_i64, _dp, _dp, c_dbl, c_dbl, c_int,
+                                ctypes.POINTER(c_int), _dp]),
+        "oracle_gpbicg": (c_int, [c_int, c_int, c_i64, _i64p, _i32p, _dp, c_i64, _dp, _dp, c_dbl, c_dbl, c_int,
+                                ctypes.POINTER(c_int), _dp]),
         "oracle_dot": (None, [c_int, c_int, c_i64, _dp, _dp, _dp, _dp]),
         "oracle_axpy": (None, [c_int, c_int, c_i64, _dp, _dp, _dp, _dp, _dp]),
         "oracle_ops_get": (ctypes.c_longlong, []),
@@ -306,3 +312,28 @@ def bicgstab(A, b, rtol, atol=0.0, maxit=1000, x0=None):
                                  A.indices.ctypes.data_as(_i32p), _d(A.data), A.data.shape[1], _d(b), _d(x), rtol,
                                  atol, maxit, ctypes.byref(it), ctypes.byref(rr))
     return st, x, it.value, rr.value
+
+
+def _krylov(name, A, b, rtol, atol, maxit, x0):
+    b = _f64(b)
+    x = np.zeros_like(b) if x0 is None else _f64(x0).copy()
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    st = getattr(_load(), name)(A.L, int(A.cplx), A.nrows, A.indptr.ctypes.data_as(_i64p),
+                                A.indices.ctypes.data_as(_i32p), _d(A.data), A.data.shape[1], _d(b), _d(x), rtol,
+                                atol, maxit, ctypes.byref(it), ctypes.byref(rr))
+    return st, x, it.value, rr.value
+
+
+def bicg(A, b, rtol, atol=0.0, maxit=1000, x0=None):
+    """BiCG (shadow products with A^H); returns (status, x, iters, relres)."""
+    return _krylov("oracle_bicg", A, b, rtol, atol, maxit, x0)
+
+
+def cgs(A, b, rtol, atol=0.0, maxit=1000, x0=None):
+    """CGS; returns (status, x, iters, relres)."""
+    return _krylov("oracle_cgs", A, b, rtol, atol, maxit, x0)
+
+
+def gpbicg(A, b, rtol, atol=0.0, maxit=1000, x0=None):
+    """GPBiCG; returns (status, x, iters, relres)."""
+    return _krylov("oracle_gpbicg", A, b, rtol, atol, maxit, x0)

@@ -668,6 +668,7 @@ static double vnorm(const vshape_t* s, const double* v) {
   vdot(s, v, v, dr, di);
   double t = 0.0;
   for (int l = s->L - 1; l >= 0; l--) t += dr[l];
+  if (isnan(t)) return t;  /* a NaN must not read as a zero norm */
   return sqrt(t > 0.0 ? t : 0.0);
 }
 
@@ -828,6 +829,312 @@ int oracle_bicgstab(int L, int cplx, int64_t n, const int64_t* indptr, const int
   *relres = bnorm > 0 ? vnorm(&s, r) / bnorm : vnorm(&s, r);
   (void)P;
   free(r); free(rh); free(p); free(v); free(sv); free(t);
+  return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* BiCG, CGS and GPBiCG: the other product-type Krylov methods of Section     */
+/* 4.2, in their textbook forms, every vector and scalar in the working       */
+/* precision, inner products (u, v) = sum conj(u_i) v_i, x0 = the given x,    */
+/* stopping test as in oracle_cg (recurrence residual).                       */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  double re[4], im[4];
+} cscal_t;
+
+static cscal_t cs_real(int L, double v) {
+  cscal_t a;
+  mp_zero(L, a.re);
+  mp_zero(L, a.im);
+  a.re[0] = v;
+  return a;
+}
+static int cs_is_zero(int L, int cplx, const cscal_t* a) {
+  return mp_is_zero(L, a->re) && (!cplx || mp_is_zero(L, a->im));
+}
+static cscal_t cs_mul(int L, int cplx, const cscal_t* a, const cscal_t* b) {
+  cscal_t r;
+  if (cplx) {
+    cmp_mul(L, a->re, a->im, b->re, b->im, r.re, r.im);
+  } else {
+    mp_mul(L, a->re, b->re, r.re);
+    mp_zero(L, r.im);
+  }
+  return r;
+}
+static cscal_t cs_div(int L, int cplx, const cscal_t* a, const cscal_t* b) {
+  cscal_t r;
+  if (cplx) {
+    cmp_div(L, a->re, a->im, b->re, b->im, r.re, r.im);
+  } else {
+    mp_div(L, a->re, b->re, r.re);
+    mp_zero(L, r.im);
+  }
+  return r;
+}
+static cscal_t cs_sub(int L, const cscal_t* a, const cscal_t* b) {
+  cscal_t r;
+  mp_sub(L, a->re, b->re, r.re);
+  mp_sub(L, a->im, b->im, r.im);
+  return r;
+}
+static cscal_t cs_neg(int L, const cscal_t* a) {
+  cscal_t r;
+  mp_neg(L, a->re, r.re);
+  mp_neg(L, a->im, r.im);
+  return r;
+}
+static cscal_t cs_conj(int L, const cscal_t* a) {
+  cscal_t r;
+  mp_copy(L, a->re, r.re);
+  mp_neg(L, a->im, r.im);
+  return r;
+}
+static cscal_t cs_dot(const vshape_t* s, const double* u, const double* v) {
+  cscal_t r;
+  vdot(s, u, v, r.re, r.im);
+  return r;
+}
+/* w := u + alpha v */
+static void cs_axpy(const vshape_t* s, const cscal_t* alpha, const double* u, const double* v, double* w) {
+  vaxpy(s, alpha->re, alpha->im, u, v, w);
+}
+/* w := a v */
+static void vscale(const vshape_t* s, const cscal_t* a, const double* v, double* w) {
+  int L = s->L;
+  for (int64_t i = 0; i < s->n; i++) {
+    double vr[4], vi[4], rr[4], ri[4];
+    vget(s, v, i, vr, vi);
+    if (s->cplx) {
+      cmp_mul(L, a->re, a->im, vr, vi, rr, ri);
+    } else {
+      mp_mul(L, a->re, vr, rr);
+    }
+    vset(s, w, i, rr, ri);
+  }
+}
+/* v := conj(v) (negate the imaginary planes) */
+static void vconj(const vshape_t* s, double* v) {
+  if (!s->cplx) return;
+  for (int64_t q = (int64_t)s->L * s->n; q < (int64_t)2 * s->L * s->n; q++) v[q] = -v[q];
+}
+
+/* y := A^H x = conj(A^T conj(x)) (the definition, through the transpose
+ * product oracle_spmtv); tmp has the size of x. */
+static void matvec_adj(const mat_t* A, const vshape_t* s, const double* x, double* y, double* tmp) {
+  size_t bytes = sizeof(double) * (size_t)((s->cplx ? 2 : 1) * s->L * s->n);
+  memcpy(tmp, x, bytes);
+  vconj(s, tmp);
+  oracle_spmtv(A->L, A->cplx, A->mixed, A->n, A->n, A->indptr, A->indices, A->data, A->dstride, tmp, A->n, y,
+               A->n);
+  vconj(s, y);
+}
+
+/* BiCG (Fletcher 1976): shadow residual r~_0 = r_0, shadow products with A^H.
+ *   q = A p, q~ = A^H p~, alpha = rho / (p~, q),
+ *   x += alpha p, r -= alpha q, r~ -= conj(alpha) q~,
+ *   rho' = (r~, r), beta = rho' / rho, p = r + beta p, p~ = r~ + conj(beta) p~. */
+int oracle_bicg(int L, int cplx, int64_t n, const int64_t* indptr, const int32_t* indices, const double* data,
+                int64_t dstride, const double* b, double* x, double rtol, double atol, int maxit, int* iters,
+                double* relres) {
+  vshape_t s = {L, cplx, n};
+  mat_t A = {L, cplx, 0, n, indptr, indices, data, dstride};
+  size_t bytes = sizeof(double) * (size_t)((cplx ? 2 : 1) * L * (n > 0 ? n : 1));
+  double *r = malloc(bytes), *rt = malloc(bytes), *p = malloc(bytes), *pt = malloc(bytes);
+  double *q = malloc(bytes), *qt = malloc(bytes), *tmp = malloc(bytes);
+  int status = OR_ENOCONV, k = 0;
+  double bnorm = vnorm(&s, b);
+  double tol = rtol * bnorm + atol;
+  residual(&A, &s, b, x, r);
+  memcpy(rt, r, bytes);
+  memcpy(p, r, bytes);
+  memcpy(pt, rt, bytes);
+  cscal_t rho = cs_dot(&s, rt, r);
+  if (vnorm(&s, r) <= tol) status = OR_OK;
+  while (status != OR_OK && k < maxit) {
+    if (cs_is_zero(L, cplx, &rho)) { status = OR_EBREAKDOWN; break; }
+    matvec(&A, p, q);
+    matvec_adj(&A, &s, pt, qt, tmp);
+    cscal_t sigma = cs_dot(&s, pt, q);
+    if (cs_is_zero(L, cplx, &sigma) || !isfinite(sigma.re[0])) { status = OR_EBREAKDOWN; break; }
+    cscal_t alpha = cs_div(L, cplx, &rho, &sigma);
+    cscal_t nalpha = cs_neg(L, &alpha);
+    cscal_t nalpha_c = cs_conj(L, &nalpha);
+    cs_axpy(&s, &alpha, x, p, x);
+    cs_axpy(&s, &nalpha, r, q, r);
+    cs_axpy(&s, &nalpha_c, rt, qt, rt);
+    k++;
+    double rn = vnorm(&s, r);
+    if (!isfinite(rn)) { status = OR_EBREAKDOWN; break; }
+    if (rn <= tol) { status = OR_OK; break; }
+    cscal_t rho1 = cs_dot(&s, rt, r);
+    cscal_t beta = cs_div(L, cplx, &rho1, &rho);
+    cscal_t beta_c = cs_conj(L, &beta);
+    cs_axpy(&s, &beta, r, p, p);
+    cs_axpy(&s, &beta_c, rt, pt, pt);
+    rho = rho1;
+  }
+  residual(&A, &s, b, x, r);
+  *iters = k;
+  *relres = bnorm > 0 ? vnorm(&s, r) / bnorm : vnorm(&s, r);
+  free(r); free(rt); free(p); free(pt); free(q); free(qt); free(tmp);
+  return status;
+}
+
+/* CGS (Sonneveld 1989), r^ = r_0:
+ *   v = A p, alpha = rho / (r^, v), q = u - alpha v, w = u + q,
+ *   x += alpha w, r -= alpha A w, rho' = (r^, r), beta = rho' / rho,
+ *   u = r + beta q, p = u + beta (q + beta p). */
+int oracle_cgs(int L, int cplx, int64_t n, const int64_t* indptr, const int32_t* indices, const double* data,
+               int64_t dstride, const double* b, double* x, double rtol, double atol, int maxit, int* iters,
+               double* relres) {
+  vshape_t s = {L, cplx, n};
+  mat_t A = {L, cplx, 0, n, indptr, indices, data, dstride};
+  size_t bytes = sizeof(double) * (size_t)((cplx ? 2 : 1) * L * (n > 0 ? n : 1));
+  double *r = malloc(bytes), *rh = malloc(bytes), *p = malloc(bytes), *u = malloc(bytes);
+  double *v = malloc(bytes), *q = malloc(bytes), *w = malloc(bytes), *t = malloc(bytes);
+  int status = OR_ENOCONV, k = 0;
+  cscal_t one = cs_real(L, 1.0);
+  double bnorm = vnorm(&s, b);
+  double tol = rtol * bnorm + atol;
+  residual(&A, &s, b, x, r);
+  memcpy(rh, r, bytes);
+  memcpy(u, r, bytes);
+  memcpy(p, r, bytes);
+  cscal_t rho = cs_dot(&s, rh, r);
+  if (vnorm(&s, r) <= tol) status = OR_OK;
+  while (status != OR_OK && k < maxit) {
+    if (cs_is_zero(L, cplx, &rho)) { status = OR_EBREAKDOWN; break; }
+    matvec(&A, p, v);
+    cscal_t sigma = cs_dot(&s, rh, v);
+    if (cs_is_zero(L, cplx, &sigma) || !isfinite(sigma.re[0])) { status = OR_EBREAKDOWN; break; }
+    cscal_t alpha = cs_div(L, cplx, &rho, &sigma);
+    cscal_t nalpha = cs_neg(L, &alpha);
+    cs_axpy(&s, &nalpha, u, v, q);
+    cs_axpy(&s, &one, u, q, w);
+    cs_axpy(&s, &alpha, x, w, x);
+    matvec(&A, w, t);
+    cs_axpy(&s, &nalpha, r, t, r);
+    k++;
+    double rn = vnorm(&s, r);
+    if (!isfinite(rn)) { status = OR_EBREAKDOWN; break; }
+    if (rn <= tol) { status = OR_OK; break; }
+    cscal_t rho1 = cs_dot(&s, rh, r);
+    cscal_t beta = cs_div(L, cplx, &rho1, &rho);
+    cs_axpy(&s, &beta, r, q, u);
+    cs_axpy(&s, &beta, q, p, p);
+    cs_axpy(&s, &beta, u, p, p);
+    rho = rho1;
+  }
+  residual(&A, &s, b, x, r);
+  *iters = k;
+  *relres = bnorm > 0 ? vnorm(&s, r) / bnorm : vnorm(&s, r);
+  free(r); free(rh); free(p); free(u); free(v); free(q); free(w); free(t);
+  return status;
+}
+
+/* GPBiCG (Zhang 1997), r^ = r_0, t_{-1} = w_{-1} = u_{-1} = z_{-1} = 0,
+ * beta_{-1} = 0.  Per iteration k:
+ *   p = r + beta (p - u), alpha = rho / (r^, A p),
+ *   y = t_prev - r - alpha w + alpha A p, t = r - alpha A p
+ *   (if ||t|| meets the test: x += alpha p and stop),
+ *   zeta, eta minimise || t - zeta A t - eta y || (eta = 0 when k = 0):
+ *     a = (At, At), b = (y, y), c = (At, y), d = (At, t), e = (y, t),
+ *     det = a b - c conj(c), zeta = (b d - c e) / det, eta = (a e - conj(c) d) / det,
+ *   u = zeta A p + eta (t_prev - r + beta u), z = zeta r + eta z - alpha u,
+ *   x += alpha p + z, r = t - eta y - zeta A t,
+ *   beta = (alpha / zeta) (r^, r_new) / (r^, r_old), w = A t + beta A p. */
+int oracle_gpbicg(int L, int cplx, int64_t n, const int64_t* indptr, const int32_t* indices,
+                  const double* data, int64_t dstride, const double* b, double* x, double rtol, double atol,
+                  int maxit, int* iters, double* relres) {
+  vshape_t s = {L, cplx, n};
+  mat_t A = {L, cplx, 0, n, indptr, indices, data, dstride};
+  size_t bytes = sizeof(double) * (size_t)((cplx ? 2 : 1) * L * (n > 0 ? n : 1));
+  double *r = malloc(bytes), *rh = malloc(bytes), *p = calloc(1, bytes), *u = calloc(1, bytes);
+  double *z = calloc(1, bytes), *w = calloc(1, bytes), *tp = calloc(1, bytes), *t = malloc(bytes);
+  double *ap = malloc(bytes), *at = malloc(bytes), *y = malloc(bytes), *tmp = malloc(bytes);
+  int status = OR_ENOCONV, k = 0;
+  const cscal_t one = cs_real(L, 1.0), mone = cs_real(L, -1.0);
+  cscal_t beta = cs_real(L, 0.0);
+  double bnorm = vnorm(&s, b);
+  double tol = rtol * bnorm + atol;
+  residual(&A, &s, b, x, r);
+  memcpy(rh, r, bytes);
+  cscal_t rho = cs_dot(&s, rh, r);
+  if (vnorm(&s, r) <= tol) status = OR_OK;
+  while (status != OR_OK && k < maxit) {
+    if (cs_is_zero(L, cplx, &rho)) { status = OR_EBREAKDOWN; break; }
+    cs_axpy(&s, &mone, p, u, tmp);            /* p = r + beta (p - u) */
+    cs_axpy(&s, &beta, r, tmp, p);
+    matvec(&A, p, ap);
+    cscal_t sigma = cs_dot(&s, rh, ap);
+    if (cs_is_zero(L, cplx, &sigma) || !isfinite(sigma.re[0])) { status = OR_EBREAKDOWN; break; }
+    cscal_t alpha = cs_div(L, cplx, &rho, &sigma);
+    cscal_t nalpha = cs_neg(L, &alpha);
+    cs_axpy(&s, &mone, tp, r, y);             /* y = t_prev - r - alpha w + alpha A p */
+    cs_axpy(&s, &nalpha, y, w, y);
+    cs_axpy(&s, &alpha, y, ap, y);
+    cs_axpy(&s, &nalpha, r, ap, t);           /* t = r - alpha A p */
+    /* t is the residual of x + alpha p: stop there when it already meets
+       the test (as BiCGSTAB stops on s); the minimisation below would
+       otherwise work on rounding-level vectors */
+    double tn = vnorm(&s, t);
+    if (!isfinite(tn)) { status = OR_EBREAKDOWN; break; }
+    if (tn <= tol) {
+      cs_axpy(&s, &alpha, x, p, x);
+      k++;
+      status = OR_OK;
+      break;
+    }
+    matvec(&A, t, at);
+    cscal_t zeta, eta;
+    if (k == 0) {
+      cscal_t d = cs_dot(&s, at, t), a = cs_dot(&s, at, at);
+      if (cs_is_zero(L, cplx, &a)) { status = OR_EBREAKDOWN; break; }
+      zeta = cs_div(L, cplx, &d, &a);
+      eta = cs_real(L, 0.0);
+    } else {
+      cscal_t a = cs_dot(&s, at, at), bb = cs_dot(&s, y, y), c = cs_dot(&s, at, y);
+      cscal_t d = cs_dot(&s, at, t), e = cs_dot(&s, y, t);
+      cscal_t cc = cs_conj(L, &c);
+      cscal_t ab = cs_mul(L, cplx, &a, &bb), c2 = cs_mul(L, cplx, &c, &cc);
+      cscal_t det = cs_sub(L, &ab, &c2);
+      if (cs_is_zero(L, cplx, &det)) { status = OR_EBREAKDOWN; break; }
+      cscal_t bd = cs_mul(L, cplx, &bb, &d), ce = cs_mul(L, cplx, &c, &e);
+      cscal_t ae = cs_mul(L, cplx, &a, &e), cd = cs_mul(L, cplx, &cc, &d);
+      cscal_t zn = cs_sub(L, &bd, &ce), en = cs_sub(L, &ae, &cd);
+      zeta = cs_div(L, cplx, &zn, &det);
+      eta = cs_div(L, cplx, &en, &det);
+    }
+    if (cs_is_zero(L, cplx, &zeta)) { status = OR_EBREAKDOWN; break; }
+    cscal_t neta = cs_neg(L, &eta), nzeta = cs_neg(L, &zeta);
+    cs_axpy(&s, &mone, tp, r, tmp);           /* u = zeta A p + eta (t_prev - r + beta u) */
+    cs_axpy(&s, &beta, tmp, u, tmp);
+    vscale(&s, &eta, tmp, tmp);
+    cs_axpy(&s, &zeta, tmp, ap, u);
+    vscale(&s, &eta, z, z);                   /* z = zeta r + eta z - alpha u */
+    cs_axpy(&s, &zeta, z, r, z);
+    cs_axpy(&s, &nalpha, z, u, z);
+    cs_axpy(&s, &alpha, x, p, x);             /* x += alpha p + z */
+    cs_axpy(&s, &one, x, z, x);
+    cs_axpy(&s, &neta, t, y, r);              /* r = t - eta y - zeta A t */
+    cs_axpy(&s, &nzeta, r, at, r);
+    k++;
+    double rn = vnorm(&s, r);
+    if (!isfinite(rn)) { status = OR_EBREAKDOWN; break; }
+    if (rn <= tol) { status = OR_OK; break; }
+    cscal_t rho1 = cs_dot(&s, rh, r);
+    cscal_t az = cs_div(L, cplx, &alpha, &zeta), rr = cs_div(L, cplx, &rho1, &rho);
+    beta = cs_mul(L, cplx, &az, &rr);
+    cs_axpy(&s, &beta, at, ap, w);            /* w = A t + beta A p */
+    memcpy(tp, t, bytes);
+    rho = rho1;
+  }
+  residual(&A, &s, b, x, r);
+  *iters = k;
+  *relres = bnorm > 0 ? vnorm(&s, r) / bnorm : vnorm(&s, r);
+  free(r); free(rh); free(p); free(u); free(z); free(w); free(tp); free(t);
+  free(ap); free(at); free(y); free(tmp);
   return status;
 }
 

@@ -28,6 +28,7 @@ MPSPMV_D, MPSPMV_DD, MPSPMV_TD, MPSPMV_QD = 1, 2, 3, 4
 MPSPMV_COMPLEX, MPSPMV_MIXED, MPSPMV_SYMMETRIC, MPSPMV_ONE_BASED = 1, 2, 4, 8
 MPSPMV_BATCH_AUTOTUNE = 1
 MPSPMV_EXACT_ACC = 16
+MPSPMV_TRANSPOSE = 32
 
 PREC = {"d": 1, "dd": 2, "td": 3, "qd": 4}
 
@@ -57,6 +58,7 @@ def _load():
         "mpspmv_destroy": [vp],
         "mpspmv_get_info": [vp, ctypes.POINTER(mpspmv_info)],
         "mpspmv_spmv": [vp, vp, vp, vp],
+        "mpspmv_spmtv": [vp, vp, vp, vp],
         "mpspmv_spmv_host": [vp, vp, vp, vp],
         "mpspmv_spmm": [vp, c_int, vp, i64, vp, i64, vp],
         "mpspmv_probe_fp64": [c_int, c_int, ctypes.POINTER(ctypes.c_double), vp],
@@ -162,6 +164,11 @@ def mpspmv_get_info(h):
 
 def mpspmv_spmv(h, x, y, stream=None):
     _check(_lib.mpspmv_spmv(h, _ptr(x), _ptr(y), _stream(stream)), "mpspmv_spmv")
+
+
+def mpspmv_spmtv(h, x, y, stream=None):
+    """y = A^T x (handle created with MPSPMV_TRANSPOSE)."""
+    _check(_lib.mpspmv_spmtv(h, _ptr(x), _ptr(y), _stream(stream)), "mpspmv_spmtv")
 
 
 def mpspmv_spmv_host(h, x_host, y_host, stream=None):

@@ -29,6 +29,7 @@ int dev_alloc(mpspmv_mat* h, T** p, int64_t count) {
 
 void free_handle(mpspmv_mat* h) {
   if (!h) return;
+  free_handle(h->tr);
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != h->device) cudaSetDevice(h->device);
@@ -106,7 +107,8 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
   *out = nullptr;
   if (nrows < 0 || ncols < 0 || nnz_in < 0 || nrows >= INT32_MAX || ncols >= INT32_MAX) return MPSPMV_EINVAL;
   if (prec < 1 || prec > 4) return MPSPMV_EINVAL;
-  if (flags & ~(MPSPMV_COMPLEX | MPSPMV_MIXED | MPSPMV_SYMMETRIC | MPSPMV_ONE_BASED | MPSPMV_EXACT_ACC))
+  if (flags & ~(MPSPMV_COMPLEX | MPSPMV_MIXED | MPSPMV_SYMMETRIC | MPSPMV_ONE_BASED | MPSPMV_EXACT_ACC |
+                MPSPMV_TRANSPOSE))
     return MPSPMV_EINVAL;
   const bool cplx = flags & MPSPMV_COMPLEX, mixed = flags & MPSPMV_MIXED;
   if (mixed && (val_limbs != 1 || prec == 1)) return MPSPMV_EINVAL;
@@ -301,6 +303,13 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
       goto fail;
     }
   }
+  // A^T: the same triplets with rows and columns swapped.  Each row of A^T
+  // lists its entries in increasing row of A (stable ordering), so a row sum
+  // of A^T adds the products in the order of the row-oriented scatter.
+  if (flags & MPSPMV_TRANSPOSE) {
+    TRY(create_impl(&h->tr, ncols, nrows, nnz_in, col, row, val, val_limbs, prec, flags & ~MPSPMV_TRANSPOSE, s));
+    h->device_bytes += h->tr->device_bytes;
+  }
 #undef TRY
   *out = h;
   return MPSPMV_OK;
@@ -372,6 +381,12 @@ int mpspmv_get_info(mpspmv_h h, mpspmv_info* info) {
 int mpspmv_spmv(mpspmv_h h, const double* x, double* y, void* stream) {
   if (!h || !x || !y) return MPSPMV_EINVAL;
   return mps_launch_spmv(h, x, y, mps_stream(stream));
+}
+
+int mpspmv_spmtv(mpspmv_h h, const double* x, double* y, void* stream) {
+  if (!h || !x || !y) return MPSPMV_EINVAL;
+  if (!h->tr) return MPSPMV_ENOTSUP;
+  return mps_launch_spmv(h->tr, x, y, mps_stream(stream));
 }
 
 int mpspmv_spmv_host(mpspmv_h h, const double* x_host, double* y_host, void* stream) {

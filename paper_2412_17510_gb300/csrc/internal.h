@@ -67,6 +67,7 @@ struct mpspmv_mat {
   struct KrylovState* d_kstate = nullptr;
   int64_t device_bytes = 0;
   std::vector<int64_t> h_indptr;  // host copy of the row offsets (re-planning)
+  mpspmv_mat* tr = nullptr;       // A^T, built from the swapped triplets (MPSPMV_TRANSPOSE)
 
   DevMat view() const {
     DevMat m;

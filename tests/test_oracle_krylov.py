@@ -163,3 +163,76 @@ def test_dot_and_axpy_against_exact(L, cplx):
             wr = ur + A_ * vr
             sc = abs(ur) + abs(A_ * vr)
         assert abs(exact.to_fraction(w[:L, i]) - wr) <= 32 * F(exact.U[L]) * sc
+
+
+# ---------------------------------------------------------------------------
+# BiCG, CGS, GPBiCG (the other product-type methods of Section 4.2)
+# ---------------------------------------------------------------------------
+def shifted_nonsym(n, L, cplx, seed):
+    coo = workloads.random_sparse(n, n, 5, seed=seed, cplx=cplx, L=1)
+    rows = np.concatenate([coo.row, np.arange(n)])
+    cols = np.concatenate([coo.col, np.arange(n)])
+    shift = np.zeros((coo.val.shape[0], n)); shift[0] = 8.0
+    if cplx:
+        shift[1] = 2.0
+    vals = np.concatenate([coo.val, shift], axis=1)
+    vv = np.zeros((vals.shape[0] * L, vals.shape[1]))
+    for c in range(vals.shape[0]):
+        vv[c * L] = vals[c]
+    return oracle.coo_to_csr(n, n, rows, cols, vv, L, cplx)
+
+
+SOLVERS = {"bicg": oracle.bicg, "cgs": oracle.cgs, "gpbicg": oracle.gpbicg}
+
+
+@pytest.mark.parametrize("method", sorted(SOLVERS))
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_product_type_methods_exact_residual_and_solution(method, L, cplx):
+    n = 30
+    A = shifted_nonsym(n, L, cplx, seed=40 + L)
+    b = workloads.full_limb_vector(n, L, seed=4, cplx=cplx)
+    st, x, it, rr = SOLVERS[method](A, b, rtol=1e-25, maxit=300)
+    assert st == 0 and 0 < it < 100
+    assert exact_residual_norm2(A, x, b) <= (F(10) ** -50) * norm2(b, L, cplx) * 4
+    assert rr <= 2e-25
+    if not cplx:
+        xs = solve_exact(dense_exact(A), [exact.to_fraction(b[:, i]) for i in range(n)])
+        err = max(abs(exact.to_fraction(x[:, i]) - xs[i]) for i in range(n))
+        assert err <= F(1, 10 ** 20)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_bicg_reduces_to_cg_on_symmetric_matrices(L):
+    """For real symmetric A and r~_0 = r_0 the shadow recurrences repeat the
+    primal ones (A^T p is the same row sum as A p), so BiCG is CG step for
+    step: same iterations, bit-identical iterates."""
+    coo = workloads.laplacian_2d(9, 7)
+    A = oracle.coo_to_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.promoted(L), L)
+    b = workloads.full_limb_vector(coo.nrows, L, seed=2)
+    st1, x1, it1, rr1 = oracle.cg(A, b, rtol=1e-20, maxit=500)
+    st2, x2, it2, rr2 = oracle.bicg(A, b, rtol=1e-20, maxit=500)
+    assert st1 == st2 == 0 and it1 == it2 and rr1 == rr2
+    assert np.array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("method", sorted(SOLVERS) + ["bicgstab"])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_finite_termination_with_few_distinct_eigenvalues(method, cplx):
+    """A diagonal matrix with m = 3 distinct eigenvalues: the Krylov space of
+    any b has dimension 3, so every method reaches the QD-level residual in at
+    most 3 iterations (the polynomial methods' termination property)."""
+    L, n = 4, 24
+    ev = [(2.0, 0.5), (3.0, -1.0), (7.0, 0.25)]
+    V = 2 if cplx else 1
+    vals = np.zeros((V * L, n))
+    for i in range(n):
+        vals[0, i] = ev[i % 3][0]
+        if cplx:
+            vals[L, i] = ev[i % 3][1]
+    A = oracle.coo_to_csr(n, n, np.arange(n), np.arange(n), vals, L, cplx)
+    b = workloads.full_limb_vector(n, L, seed=9, cplx=cplx)
+    solver = oracle.bicgstab if method == "bicgstab" else SOLVERS[method]
+    st, x, it, rr = solver(A, b, rtol=1e-50, maxit=10)
+    assert st == 0 and it <= 3
+    assert exact_residual_norm2(A, x, b) <= (F(10) ** -98) * norm2(b, L, cplx)

@@ -199,6 +199,29 @@ int mpspmv_bicgstab(mpspmv_h h, const double* b, double* x, double rtol, double 
                     double* relres, void* stream);
 
 /*
+ * mpspmv_bicg, mpspmv_cgs, mpspmv_gpbicg -- the other product-type Krylov
+ * methods of Section 4.2 (BiCG, CGS and GPBiCG on tub1000), real or complex,
+ * every vector and scalar in the handle's precision; arguments, stopping
+ * test and returns as mpspmv_cg.
+ *   BiCG (Fletcher): shadow residual r~_0 = r_0, shadow products with A^H.
+ *     Requires a handle created with MPSPMV_TRANSPOSE (MPSPMV_ENOTSUP
+ *     otherwise).  Complex data keep the shadow vectors conjugated, so the
+ *     shadow product is mpspmv_spmtv of a conjugated vector.
+ *   CGS (Sonneveld): r^ = r_0.
+ *   GPBiCG (Zhang): r^ = r_0; the iteration also stops, after x += alpha p,
+ *     when ||t_k|| = ||r_k - alpha A p_k|| meets the test (t_k is the
+ *     residual of that iterate).
+ * MPSPMV_EXACT_ACC handles use the exact vector arithmetic of mpspmv_dot /
+ * mpspmv_axpy.  Synchronise `stream` before returning.
+ */
+int mpspmv_bicg(mpspmv_h h, const double* b, double* x, double rtol, double atol, int maxit, int* iters,
+                double* relres, void* stream);
+int mpspmv_cgs(mpspmv_h h, const double* b, double* x, double rtol, double atol, int maxit, int* iters,
+               double* relres, void* stream);
+int mpspmv_gpbicg(mpspmv_h h, const double* b, double* x, double rtol, double atol, int maxit, int* iters,
+                  double* relres, void* stream);
+
+/*
  * Krylov vector operations in the handle's precision and arithmetic (the
  * inner products and vector updates of Section 4.2's CG and BiCGSTAB, with
  * every vector and scalar in DD / TD / QD).  The handle supplies L, real or

@@ -373,14 +373,26 @@ static void cmp_mul(int L, const double* ar, const double* ai, const double* br,
   mp_sub(L, t1, t2, rr);
   mp_add(L, t3, t4, ri);
 }
-/* (a/b) = a*conj(b)/|b|^2 */
+/* (a/b) = a*conj(b)/|b|^2, with a and b first scaled by the same power of
+ * two (exact, component by component) so that the larger part of b is near
+ * 1: |b|^2 then stays in range when b is tiny or huge (scalars of a
+ * converged Krylov iteration reach 1e-200 and below). */
 static void cmp_div(int L, const double* ar, const double* ai, const double* br, const double* bi,
                     double* rr, double* ri) {
   double nbi[4], nr[4], ni[4], d[4], t1[4], t2[4];
-  mp_neg(L, bi, nbi);
-  cmp_mul(L, ar, ai, br, nbi, nr, ni);
-  mp_mul(L, br, br, t1);
-  mp_mul(L, bi, bi, t2);
+  double as_r[4], as_i[4], bs_r[4], bs_i[4];
+  double m = fmax(fabs(br[0]), fabs(bi[0]));
+  int e = (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
+  for (int l = 0; l < L; l++) {
+    as_r[l] = scalbn(ar[l], -e);
+    as_i[l] = scalbn(ai[l], -e);
+    bs_r[l] = scalbn(br[l], -e);
+    bs_i[l] = scalbn(bi[l], -e);
+  }
+  mp_neg(L, bs_i, nbi);
+  cmp_mul(L, as_r, as_i, bs_r, nbi, nr, ni);
+  mp_mul(L, bs_r, bs_r, t1);
+  mp_mul(L, bs_i, bs_i, t2);
   mp_add(L, t1, t2, d);
   mp_div(L, nr, d, rr);
   mp_div(L, ni, d, ri);

@@ -68,6 +68,12 @@ def _load():
                             ctypes.POINTER(ctypes.c_double), vp],
         "mpspmv_dot": [vp, i64, vp, vp, vp, vp],
         "mpspmv_axpy": [vp, i64, vp, vp, vp, vp, vp],
+        "mpspmv_bicg": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
+                        ctypes.POINTER(ctypes.c_double), vp],
+        "mpspmv_cgs": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
+                       ctypes.POINTER(ctypes.c_double), vp],
+        "mpspmv_gpbicg": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
+                          ctypes.POINTER(ctypes.c_double), vp],
         "mpspmv_spmv_csr_noalloc": [c_int, ctypes.c_uint, i64, i64, i64, vp, vp, vp, vp, vp, vp],
         "mpspmv_batch_create": [vp, vp, c_int, ctypes.c_uint, ctypes.POINTER(vp), vp],
         "mpspmv_batch_destroy": [vp],
@@ -195,6 +201,22 @@ def mpspmv_cg(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=
 def mpspmv_bicgstab(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=False):
     """BiCGSTAB in place on x.  Returns (status, iterations, true relative residual)."""
     return _solve(_lib.mpspmv_bicgstab, "mpspmv_bicgstab", h, b, x, rtol, atol, maxit, stream, raise_on_noconv)
+
+
+def mpspmv_bicg(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=False):
+    """BiCG in place on x (handle created with MPSPMV_TRANSPOSE).  Returns
+    (status, iterations, true relative residual)."""
+    return _solve(_lib.mpspmv_bicg, "mpspmv_bicg", h, b, x, rtol, atol, maxit, stream, raise_on_noconv)
+
+
+def mpspmv_cgs(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=False):
+    """CGS in place on x.  Returns (status, iterations, true relative residual)."""
+    return _solve(_lib.mpspmv_cgs, "mpspmv_cgs", h, b, x, rtol, atol, maxit, stream, raise_on_noconv)
+
+
+def mpspmv_gpbicg(h, b, x, rtol, atol=0.0, maxit=1000, stream=None, raise_on_noconv=False):
+    """GPBiCG in place on x.  Returns (status, iterations, true relative residual)."""
+    return _solve(_lib.mpspmv_gpbicg, "mpspmv_gpbicg", h, b, x, rtol, atol, maxit, stream, raise_on_noconv)
 
 
 def mpspmv_dot(h, n, u, v, stream=None):

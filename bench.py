@@ -205,6 +205,12 @@ def run_reference(args):
     import multiprocessing as mp
     ncores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
+    if args.cg_only:
+        # profiling entry: one CG variant, no timed SpMV step
+        out = suite_cg(mps, torch.cuda.current_stream(), args.small, only=args.cg_only, its=args.cg_iters)
+        print(json.dumps(out))
+        return
+
     mats = make_matrices(args.small)
     xs = {m: {L: workloads.full_limb_vector(c.ncols, L, seed=0) for L in PRECS} for m, c in mats.items()}
     nnz_of = {(m, L): c.nnz for m, c in mats.items() for L in PRECS}
@@ -303,19 +309,21 @@ def suite_complex(mps, fp64_fma, hbm, stream, small):
     return out
 
 
-def suite_cg(mps, stream, small):
+def suite_cg(mps, stream, small, only=None, its=200):
     """CG on the SPD 7-point diffusion matrix on a 128^3 grid (kappa
-    log-uniform in [0.1, 10]), a fixed 200 iterations (rtol = 0), paper-order
+    log-uniform in [0.1, 10]), a fixed number of iterations (rtol = 0; 200 by
+    default), paper-order
     and exact-accumulation handles: ms per iteration, and the SpMV's ms for
     comparison (the rest is the vector kernels and the scalar steps)."""
     import torch
     N = 48 if small else 128
     coo = workloads.diffusion_7pt(N, N, N, kappa_range=(0.1, 10.0), seed=0)
     n = coo.nrows
-    out = {"workload": "7-point diffusion %d^3 (n=%d, nnz=%d), 200 CG iterations" % (N, n, coo.nnz)}
-    its = 200
+    out = {"workload": "7-point diffusion %d^3 (n=%d, nnz=%d), %d CG iterations" % (N, n, coo.nnz, its)}
     for L in (2, 3, 4):
         for arith, fl in (("paper", 0), ("exact", 16)):
+            if only and only != "%s/%s" % (PNAME[L], arith):
+                continue
             h = mps.mpspmv_create_csr(n, n, coo.row, coo.col, coo.val, L, fl, val_limbs=1)
             b = torch.from_numpy(workloads.full_limb_vector(n, L, seed=1)).cuda()
             x = torch.zeros_like(b)
@@ -334,6 +342,38 @@ def suite_cg(mps, stream, small):
                                                    "relres": rr, "status": st}
             mps.mpspmv_destroy(h)
             del b, x, y
+    return out
+
+
+def suite_product(mps, stream, small):
+    """The product-type methods of Section 4.2 (BiCG, CGS, BiCGSTAB, GPBiCG)
+    on a nonsymmetric band matrix: 2D convection-diffusion 300 x 300 (c = 0.5,
+    n = 90,000), b = A x_true, x0 = 0, DD to 1e-25 and QD to 1e-50, paper-order
+    and exact arithmetic: iterations, seconds, true relative residual."""
+    import torch
+    N = 100 if small else 300
+    coo = workloads.convection_diffusion_2d(N, N, 0.5)
+    n = coo.nrows
+    out = {"workload": "convection-diffusion 2D %dx%d (n=%d, nnz=%d)" % (N, N, n, coo.nnz)}
+    methods = (("bicg", mps.mpspmv_bicg), ("cgs", mps.mpspmv_cgs), ("bicgstab", mps.mpspmv_bicgstab),
+               ("gpbicg", mps.mpspmv_gpbicg))
+    for L, rtol in ((2, 1e-25), (4, 1e-50)):
+        for arith, fl in (("paper", 0), ("exact", 16)):
+            h = mps.mpspmv_create_csr(n, n, coo.row, coo.col, coo.val, L, fl | mps.MPSPMV_TRANSPOSE, val_limbs=1)
+            xt = torch.from_numpy(workloads.full_limb_vector(n, L, seed=2)).cuda()
+            b = torch.empty_like(xt)
+            mps.mpspmv_spmv(h, xt, b, stream)
+            for name, fn in methods:
+                x = torch.zeros_like(b)
+                fn(h, b, x, rtol, 0.0, 8, stream)  # workspace and graph warm-up
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, it, rr = fn(h, b, x, rtol, 0.0, 20000, stream)
+                torch.cuda.synchronize()
+                out["%s_%s_%s" % (name, PNAME[L], arith)] = {"status": st, "iters": it, "relres": rr,
+                                                             "s": time.perf_counter() - t0}
+            mps.mpspmv_destroy(h)
     return out
 
 
@@ -444,8 +484,12 @@ def main():
                     help="paper: the paper's DD/TD/QD operation sequences; exact: error-free products on the "
                          "binary64 pipe with exact integer accumulation (MPSPMV_EXACT_ACC); both: value from "
                          "exact, the paper-order step timed too")
-    ap.add_argument("--suite", nargs="?", const="complex,cg,batched,selector", default=None,
-                    help="also measure the complex, CG, batched and selector workloads (adds minutes); "
+    ap.add_argument("--cg-only", default=None,
+                    help="profiling: run only the CG workload of the suite in one variant, e.g. QD/exact, and exit")
+    ap.add_argument("--cg-iters", type=int, default=200, help="CG iterations of the CG workload")
+    ap.add_argument("--suite", nargs="?", const="complex,cg,product,batched,selector", default=None,
+                    help="also measure the complex, CG, product-type, batched and selector workloads (adds "
+                         "minutes); "
                          "optionally a comma-separated subset")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -644,6 +688,7 @@ def main():
         del flush
         parts = {"complex": lambda: suite_complex(mps, fp64_fma, hbm, stream, args.small),
                  "cg": lambda: suite_cg(mps, stream, args.small),
+                 "product": lambda: suite_product(mps, stream, args.small),
                  "batched": lambda: suite_batched(mps, stream, args.small),
                  "selector": lambda: suite_selector(mps, args.small)}
         suite = {}

@@ -98,6 +98,27 @@ def laplacian_2d(nx, ny=None):
     return _sorted_coo(n, n, rows, cols, vals, "laplace2d_%dx%d" % (nx, ny))
 
 
+def convection_diffusion_2d(nx, ny=None, c=0.5):
+    """2D 5-point convection-diffusion, -Laplace(u) + b . grad(u) with
+    centred convection on a unit-spaced grid: diagonal 4, west/south -1 - c,
+    east/north -1 + c (|c| < 1 keeps it an M-matrix).  Nonsymmetric band
+    matrix (half-bandwidth nx), a stand-in for the nonsymmetric band
+    matrices of the product-type Krylov comparison."""
+    ny = nx if ny is None else ny
+    n = nx * ny
+    idx = np.arange(n).reshape(ny, nx)
+    rows, cols, vals = [], [], []
+    for dy, dx, v in ((-1, 0, -1.0 - c), (0, -1, -1.0 - c), (0, 0, 4.0), (0, 1, -1.0 + c), (1, 0, -1.0 + c)):
+        ys, xs = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        ok = (ys + dy >= 0) & (ys + dy < ny) & (xs + dx >= 0) & (xs + dx < nx)
+        r = idx[ok]
+        cc = idx[(ys + dy)[ok], (xs + dx)[ok]]
+        rows.append(r)
+        cols.append(cc)
+        vals.append(np.full(r.shape, v))
+    return _sorted_coo(n, n, rows, cols, vals, "convdiff2d_%dx%d_c%g" % (nx, ny, c))
+
+
 def _sorted_coo(nr, nc, rows, cols, vals, name):
     r = np.concatenate(rows)
     c = np.concatenate(cols)

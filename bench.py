@@ -414,8 +414,9 @@ def suite_batched(mps, stream, small):
     cspecs = workloads.batch_specs(8 if small else 32, n_range=(1000, 10000), k_range=(1, 8), seed=1)
     ccoos = [workloads.diffusion_7pt(nx, ny, nz, seed=sd) for nx, ny, nz, k, sd in cspecs]
     cks = [k for *_, k, sd in cspecs]
-    for L in (2, 4):
-        hs = [mps.mpspmv_create_csr(c.nrows, c.ncols, c.row, c.col, c.val, L, 0, val_limbs=1) for c in ccoos]
+    for L, arith in ((2, "paper"), (2, "exact"), (4, "paper"), (4, "exact")):
+        fl = 16 if arith == "exact" else 0
+        hs = [mps.mpspmv_create_csr(c.nrows, c.ncols, c.row, c.col, c.val, L, fl, val_limbs=1) for c in ccoos]
         b = mps.mpspmv_batch_create(hs, cks, 0, stream)
         Bs = [torch.from_numpy(np.ascontiguousarray(np.stack(
             [workloads.full_limb_vector(c.ncols, L, seed=100 + i * 40 + j) for j in range(k)], axis=-1))).cuda()
@@ -425,7 +426,7 @@ def suite_batched(mps, stream, small):
         t0 = time.perf_counter()
         st, it, rr, ss = mps.mpspmv_batch_cg(b, Bs, Xs, sum(cks), 1e-25, 0.0, 100000, stream)
         torch.cuda.synchronize()
-        out["cg_%s" % PNAME[L]] = {"systems": int(sum(cks)), "s": time.perf_counter() - t0, "status": st,
+        out["cg_%s%s" % (PNAME[L], "_exact" if fl else "")] = {"systems": int(sum(cks)), "s": time.perf_counter() - t0, "status": st,
                                    "converged": int((ss == 0).sum()), "iters_max": int(it.max()),
                                    "iters_mean": float(it.mean()), "relres_max": float(rr.max())}
         mps.mpspmv_batch_destroy(b)

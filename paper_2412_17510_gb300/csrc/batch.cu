@@ -264,10 +264,197 @@ __global__ void __launch_bounds__(kBT) batch_vec_kernel(const BatchEntry* __rest
   }
 }
 
+// ---------------------------------------------------------------------------
+// Exact-accumulation variant of the batched CG vector kernels (batches of
+// handles created with MPSPMV_EXACT_ACC): each updated element is formed from
+// its terms' components and error-free products in one exact accumulator and
+// cut once; each thread sums its share of an inner product exactly; the
+// threads of one right-hand side are then added on fixed-point digits at
+// their common base, and the finishing step adds the block partials exactly.
+// Blocks of kBTX threads; accumulator a of a thread uses 2 D digits of the
+// block's dynamic shared memory (digit j of thread t at j kBTX + t).
+// ---------------------------------------------------------------------------
+constexpr int kBTX = 128;
+
+template <int L>
+using BAcc = FixAccS<AccDigits<L>::D, kBTX>;
+
+template <int L>
+constexpr size_t bx_smem(int nacc) {
+  return (size_t)nacc * 2 * AccDigits<L>::D * kBTX * sizeof(unsigned long long);
+}
+
+template <int L>
+__device__ __forceinline__ BAcc<L> bx_acc(unsigned long long* digits, int a) {
+  constexpr int D = AccDigits<L>::D;
+  BAcc<L> r;
+  r.dp = digits + (size_t)a * 2 * D * kBTX + threadIdx.x;
+  r.dn = r.dp + D * kBTX;
+  fas_reset<D, kBTX>(r);
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ mp<L> bx_flush(BAcc<L>& a) {
+  mp<L> r;
+  fas_to_mp<L, AccDigits<L>::D, kBTX>(a, r.v);
+  fas_reset<AccDigits<L>::D, kBTX>(a);
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ void bx_add(BAcc<L>& a, const mp<L>& u, bool neg) {
+#pragma unroll
+  for (int l = 0; l < L; l++) acc_add(a, u.v[l], neg);
+}
+
+// Exact sum over the threads of each right-hand side (threads rhs, rhs + kp,
+// ...) of one MP value per thread; thread rhs < kp writes the partial of
+// block vb: part[(vb * 32 + rhs) * L + l].
+template <int L>
+__device__ __forceinline__ void block_rhs_reduce_x(const mp<L>& v, int kp, double* __restrict__ part, int64_t vb) {
+  constexpr int D = AccDigits<L>::D, NW = kBTX / 32;
+  __shared__ int s_top[NW][32];
+  __shared__ int s_bad[NW][32];
+  __shared__ long long s_d[NW][32][D];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int t = INT_MIN, bad = 0;
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    t = max(t, top_exp(v.v[l]));
+    bad |= isfinite(v.v[l]) ? 0 : 1;
+  }
+  // lanes with the same right-hand side differ by multiples of kp
+  for (int off = 16; off >= kp; off >>= 1) {
+    t = max(t, __shfl_xor_sync(0xffffffffu, t, off));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+  if (lane < kp) {
+    s_top[warp][lane] = t;
+    s_bad[warp][lane] = bad;
+  }
+  __syncthreads();
+  const int rhs = lane & (kp - 1);
+  t = s_top[0][rhs];
+  for (int w = 1; w < NW; w++) t = max(t, s_top[w][rhs]);
+  FixAcc<D> f;
+  fa_at_top<D>(f, t);
+#pragma unroll
+  for (int l = 0; l < L; l++) fa_add<D>(f, v.v[l]);
+#pragma unroll
+  for (int j = 0; j < D; j++)
+    for (int off = 16; off >= kp; off >>= 1) f.d[j] += __shfl_down_sync(0xffffffffu, f.d[j], off);
+  if (lane < kp) {
+#pragma unroll
+    for (int j = 0; j < D; j++) s_d[warp][lane][j] = f.d[j];
+  }
+  __syncthreads();
+  if (threadIdx.x < kp) {
+    FixAcc<D> r;
+    fa_at_top<D>(r, t);
+    for (int w = 0; w < NW; w++) {
+#pragma unroll
+      for (int j = 0; j < D; j++) r.d[j] += s_d[w][threadIdx.x][j];
+      r.bad |= s_bad[w][threadIdx.x] != 0;
+    }
+    double out[L];
+    fa_to_mp<L, D>(r, out);
+#pragma unroll
+    for (int l = 0; l < L; l++) part[(vb * 32 + threadIdx.x) * L + l] = out[l];
+  }
+  __syncthreads();
+}
+
+// Same operations and vector roles as batch_vec_kernel.
+template <int L, int OP>
+__global__ void __launch_bounds__(kBTX) batch_vec_kernel_x(const BatchEntry* __restrict__ E,
+                                                           const int64_t* __restrict__ vstart, int nm, CgSys S,
+                                                           double* const* __restrict__ vec, int i0, int i1, int i2,
+                                                           int i3, double* __restrict__ part,
+                                                           double* __restrict__ part2, bool gate) {
+  extern __shared__ unsigned long long bx_digits[];
+  const int64_t vb = blockIdx.x;
+  const int e = find_entry(vstart, nm, vb);
+  const BatchEntry* be = E + e;
+  const int kp = be->kp, k = be->k;
+  const int64_t n = be->m.nrows, ld = be->ldx;
+  const int64_t plane = n * ld;
+  const int64_t r0 = (vb - __ldg(vstart + e)) * kRB;
+  const int rhs = threadIdx.x & (kp - 1);
+  const int stripe = threadIdx.x / kp, nstripe = kBTX / kp;
+  const int64_t sys = be->sys0 + rhs;
+  const bool live = rhs < k && (!gate || S.status[sys] == 0);
+  double* v0 = vec[(int64_t)e * 8 + i0];
+  double* v1 = vec[(int64_t)e * 8 + i1];
+  double* v2 = vec[(int64_t)e * 8 + i2];
+  double* v3 = vec[(int64_t)e * 8 + i3];
+  // accumulators: 0 element, 1 first inner product, 2 second (V_RESID)
+  BAcc<L> el, d1, d2;
+  if (OP != V_DOT) el = bx_acc<L>(bx_digits, 0);
+  if (OP != V_P) d1 = bx_acc<L>(bx_digits, OP == V_DOT ? 0 : 1);
+  if (OP == V_RESID) d2 = bx_acc<L>(bx_digits, 2);
+  mp<L> al, be_;
+  if (live && OP == V_XR) al = lds<L>(S.alpha, sys);
+  if (live && OP == V_P) be_ = lds<L>(S.beta, sys);
+  if (live) {
+    const int64_t rend = min(r0 + kRB, n);
+    for (int64_t r = r0 + stripe; r < rend; r += nstripe) {
+      const int64_t idx = r * ld + rhs;
+      if (OP == V_RESID) {  // v0 = b, v1 = q (A x), v2 = r, v3 = p
+        const mp<L> b = ldv<L>(v0, plane, idx);
+        bx_add<L>(el, b, false);
+        bx_add<L>(el, ldv<L>(v1, plane, idx), true);
+        const mp<L> ri = bx_flush<L>(el);
+        stv<L>(v2, plane, idx, ri);
+        if (v3) stv<L>(v3, plane, idx, ri);
+        add_prod<BAcc<L>, L>(d1, ri, ri, false);
+        add_prod<BAcc<L>, L>(d2, b, b, false);
+      } else if (OP == V_DOT) {  // (v0, v1)
+        add_prod<BAcc<L>, L>(d1, ldv<L>(v0, plane, idx), ldv<L>(v1, plane, idx), false);
+      } else if (OP == V_XR) {  // v0 = x, v1 = r, v2 = p, v3 = q
+        bx_add<L>(el, ldv<L>(v0, plane, idx), false);
+        add_prod<BAcc<L>, L>(el, al, ldv<L>(v2, plane, idx), false);
+        stv<L>(v0, plane, idx, bx_flush<L>(el));
+        bx_add<L>(el, ldv<L>(v1, plane, idx), false);
+        add_prod<BAcc<L>, L>(el, al, ldv<L>(v3, plane, idx), true);
+        const mp<L> ri = bx_flush<L>(el);
+        stv<L>(v1, plane, idx, ri);
+        add_prod<BAcc<L>, L>(d1, ri, ri, false);
+      } else {  // V_P: v0 = r, v1 = p
+        bx_add<L>(el, ldv<L>(v0, plane, idx), false);
+        add_prod<BAcc<L>, L>(el, be_, ldv<L>(v1, plane, idx), false);
+        stv<L>(v1, plane, idx, bx_flush<L>(el));
+      }
+    }
+  }
+  if (OP != V_P) {
+    block_rhs_reduce_x<L>(bx_flush<L>(d1), kp, part, vb);
+    if (OP == V_RESID) block_rhs_reduce_x<L>(bx_flush<L>(d2), kp, part2, vb);
+  }
+}
+
+// exact sum of the nb block partials of one system (thread per system)
+template <int L>
+__device__ __forceinline__ mp<L> sum_partials_x(const double* __restrict__ part, int64_t vb0, int64_t nb, int rhs) {
+  constexpr int D = AccDigits<L>::D;
+  int t = INT_MIN;
+  for (int64_t j = 0; j < nb; j++)
+#pragma unroll
+    for (int l = 0; l < L; l++) t = max(t, top_exp(part[((vb0 + j) * 32 + rhs) * L + l]));
+  FixAcc<D> f;
+  fa_at_top<D>(f, t);
+  for (int64_t j = 0; j < nb; j++)
+#pragma unroll
+    for (int l = 0; l < L; l++) fa_add<D>(f, part[((vb0 + j) * 32 + rhs) * L + l]);
+  mp<L> r;
+  fa_to_mp<L, D>(f, r.v);
+  return r;
+}
+
 // Per-system finishing steps (thread per system).
 enum FinOp { F_START = 0, F_ALPHA = 1, F_BETA = 2, F_RELRES = 3 };
 
-template <int L, int OP>
+template <int L, int OP, bool EX = false>
 __global__ void batch_finish_kernel(const BatchEntry* __restrict__ E, const int64_t* __restrict__ sstart, int nm,
                                     int64_t nsys, CgSys S, const double* __restrict__ part,
                                     const double* __restrict__ part2, double rtol, double atol, int maxit) {
@@ -279,9 +466,14 @@ __global__ void batch_finish_kernel(const BatchEntry* __restrict__ E, const int6
   const int rhs = (int)(sys - be->sys0);
   const int64_t nb = (be->m.nrows + kRB - 1) / kRB;
   mp<L> a = mp_zero<L>(), b = mp_zero<L>();
-  for (int64_t j = 0; j < nb; j++) {
-    a = mp_add<L>(a, ldv<L>(part, 1, ((be->vb0 + j) * 32 + rhs) * L));
-    if (OP == F_START) b = mp_add<L>(b, ldv<L>(part2, 1, ((be->vb0 + j) * 32 + rhs) * L));
+  if (EX) {
+    a = sum_partials_x<L>(part, be->vb0, nb, rhs);
+    if (OP == F_START) b = sum_partials_x<L>(part2, be->vb0, nb, rhs);
+  } else {
+    for (int64_t j = 0; j < nb; j++) {
+      a = mp_add<L>(a, ldv<L>(part, 1, ((be->vb0 + j) * 32 + rhs) * L));
+      if (OP == F_START) b = mp_add<L>(b, ldv<L>(part2, 1, ((be->vb0 + j) * 32 + rhs) * L));
+    }
   }
   if (OP == F_START) {  // a = (r, r), b = (b, b)
     const double bb = mp_to_double<L>(b), rr = mp_to_double<L>(a);
@@ -567,6 +759,41 @@ int autotune(mpspmv_batch* b, cudaStream_t s) {
   return st;
 }
 
+// Launch the paper-order or the exact batched vector kernel.
+template <int L, int OP>
+int launch_vec(bool ex, unsigned nvb, cudaStream_t s, const mpspmv_batch* b, int n, const CgSys& S, int i0, int i1,
+               int i2, int i3, double* part, double* part2, bool gate) {
+  if (!ex) {
+    batch_vec_kernel<L, OP><<<nvb, kBT, 0, s>>>(b->d_entries, b->d_vec_start, n, S, b->d_vecs, i0, i1, i2, i3, part,
+                                                part2, gate);
+    return MPSPMV_OK;
+  }
+  constexpr int nacc = OP == V_RESID ? 3 : (OP == V_XR ? 2 : 1);
+  static bool attr = false;  // the residual kernel's three accumulators exceed the default 48 KB
+  if (!attr) {
+    if (cudaFuncSetAttribute(batch_vec_kernel_x<L, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bx_smem<L>(nacc)) != cudaSuccess) {
+      cudaGetLastError();
+      return MPSPMV_ECUDA;
+    }
+    attr = true;
+  }
+  batch_vec_kernel_x<L, OP><<<nvb, kBTX, bx_smem<L>(nacc), s>>>(b->d_entries, b->d_vec_start, n, S, b->d_vecs, i0, i1,
+                                                               i2, i3, part, part2, gate);
+  return MPSPMV_OK;
+}
+
+template <int L, int OP>
+void launch_fin(bool ex, unsigned fin, cudaStream_t s, const mpspmv_batch* b, int n, const CgSys& S,
+                const double* part, const double* part2, double rtol, double atol, int maxit) {
+  if (ex)
+    batch_finish_kernel<L, OP, true><<<fin, 128, 0, s>>>(b->d_entries, b->d_sys_start, n, b->nsys, S, part, part2,
+                                                         rtol, atol, maxit);
+  else
+    batch_finish_kernel<L, OP, false><<<fin, 128, 0, s>>>(b->d_entries, b->d_sys_start, n, b->nsys, S, part, part2,
+                                                          rtol, atol, maxit);
+}
+
 template <int L>
 int batch_cg_impl(mpspmv_batch* b, const double* const* B, const int64_t* ldb, double* const* X,
                   const int64_t* ldx, double rtol, double atol, int maxit, int* iters, double* relres,
@@ -640,12 +867,11 @@ int batch_cg_impl(mpspmv_batch* b, const double* const* B, const int64_t* ldb, d
   if ((st = enqueue_spmm<L>(b, nullptr, s))) return st;
   const unsigned nvb = (unsigned)b->nvb;
   const unsigned fin = (unsigned)((b->nsys + 127) / 128);
+  const bool ex = b->mats[0]->exact;  // the batch's handles share the arithmetic
   CgSys S = b->sys;
   // r = b - q, p = r, (r, r), (b, b), per-system start
-  batch_vec_kernel<L, V_RESID><<<nvb, kBT, 0, s>>>(b->d_entries, b->d_vec_start, n, S, b->d_vecs, 0, 4, 2, 3, part,
-                                                   part2, false);
-  batch_finish_kernel<L, F_START><<<fin, 128, 0, s>>>(b->d_entries, b->d_sys_start, n, b->nsys, S, part, part2,
-                                                      rtol, atol, maxit);
+  if ((st = launch_vec<L, V_RESID>(ex, nvb, s, b, n, S, 0, 4, 2, 3, part, part2, false))) return st;
+  launch_fin<L, F_START>(ex, fin, s, b, n, S, part, part2, rtol, atol, maxit);
   MPS_CUDA(cudaGetLastError());
   // iterations: SpMM now reads p and writes q
   for (int i = 0; i < n; i++) pin[i] = vt[i * 8 + 3];
@@ -662,16 +888,11 @@ int batch_cg_impl(mpspmv_batch* b, const double* const* B, const int64_t* ldb, d
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = MPSPMV_ECUDA;
   for (int it = 0; it < kCgItersPerGraph && !st; it++) {
     st = enqueue_spmm<L>(b, S.status, cs);
-    batch_vec_kernel<L, V_DOT><<<nvb, kBT, 0, cs>>>(b->d_entries, b->d_vec_start, n, S, b->d_vecs, 3, 4, 0, 0, part,
-                                                    nullptr, true);
-    batch_finish_kernel<L, F_ALPHA><<<fin, 128, 0, cs>>>(b->d_entries, b->d_sys_start, n, b->nsys, S, part, nullptr,
-                                                         rtol, atol, maxit);
-    batch_vec_kernel<L, V_XR><<<nvb, kBT, 0, cs>>>(b->d_entries, b->d_vec_start, n, S, b->d_vecs, 1, 2, 3, 4, part,
-                                                   nullptr, true);
-    batch_finish_kernel<L, F_BETA><<<fin, 128, 0, cs>>>(b->d_entries, b->d_sys_start, n, b->nsys, S, part, nullptr,
-                                                        rtol, atol, maxit);
-    batch_vec_kernel<L, V_P><<<nvb, kBT, 0, cs>>>(b->d_entries, b->d_vec_start, n, S, b->d_vecs, 2, 3, 0, 0, part,
-                                                  nullptr, true);
+    if (!st) st = launch_vec<L, V_DOT>(ex, nvb, cs, b, n, S, 3, 4, 0, 0, part, nullptr, true);
+    launch_fin<L, F_ALPHA>(ex, fin, cs, b, n, S, part, nullptr, rtol, atol, maxit);
+    if (!st) st = launch_vec<L, V_XR>(ex, nvb, cs, b, n, S, 1, 2, 3, 4, part, nullptr, true);
+    launch_fin<L, F_BETA>(ex, fin, cs, b, n, S, part, nullptr, rtol, atol, maxit);
+    if (!st) st = launch_vec<L, V_P>(ex, nvb, cs, b, n, S, 2, 3, 0, 0, part, nullptr, true);
     if (cudaGetLastError() != cudaSuccess) st = MPSPMV_ECUDA;
   }
   cudaError_t ee = cudaStreamEndCapture(cs, &g);
@@ -700,10 +921,8 @@ int batch_cg_impl(mpspmv_batch* b, const double* const* B, const int64_t* ldb, d
   for (int i = 0; i < n; i++) tout[i] = vt[i * 8 + 5];
   if ((st = set_vectors(b, xin.data(), nullptr, qout.data(), nullptr, s))) return st;
   if ((st = enqueue_spmm<L>(b, nullptr, s))) return st;
-  batch_vec_kernel<L, V_RESID><<<nvb, kBT, 0, s>>>(b->d_entries, b->d_vec_start, n, S, b->d_vecs, 0, 4, 5, 7, part,
-                                                   part2, false);
-  batch_finish_kernel<L, F_RELRES><<<fin, 128, 0, s>>>(b->d_entries, b->d_sys_start, n, b->nsys, S, part, part2,
-                                                       rtol, atol, maxit);
+  if ((st = launch_vec<L, V_RESID>(ex, nvb, s, b, n, S, 0, 4, 5, 7, part, part2, false))) return st;
+  launch_fin<L, F_RELRES>(ex, fin, s, b, n, S, part, part2, rtol, atol, maxit);
   MPS_CUDA(cudaGetLastError());
   std::vector<int> hit(b->nsys);
   std::vector<double> hrr(b->nsys);

@@ -19,6 +19,7 @@
 // the carries are propagated once and the value is cut into L binary64
 // components by truncation (value = sum of components to 53 L bits).
 #pragma once
+#include <climits>
 #include <stdint.h>
 
 namespace mpk {
@@ -199,12 +200,16 @@ __device__ __forceinline__ void fa_to_mp(const FixAcc<D>& a, double* out) {
 // ---------------------------------------------------------------------------
 namespace mpk {
 
+// Base of an accumulator that has not received a term yet: every term then
+// lands far above the window and takes the out-of-line window path, which
+// anchors the window at that term.  (e0 - kNotLive stays below 2^31.)
+constexpr int kNotLive = -(1 << 30);
+
 template <int D, int T>
 struct FixAccS {
   unsigned long long* dp;  // this thread's digit 0 of the positive terms; digit j at dp[j * T]
   unsigned long long* dn;  // ... of the negative terms
-  int base;
-  bool live;
+  int base;                // kNotLive until the first non-zero term
   bool bad;
 };
 
@@ -215,8 +220,7 @@ __device__ __forceinline__ void fas_reset(FixAccS<D, T>& a) {
     a.dp[j * T] = 0;
     a.dn[j * T] = 0;
   }
-  a.base = 0;
-  a.live = false;
+  a.base = kNotLive;
   a.bad = false;
 }
 
@@ -238,44 +242,81 @@ __device__ __noinline__ void fas_shift_smem(unsigned long long* d, int s) {
   }
 }
 
-// a += v (neg: a -= v)
+// The window for a term whose top bit (e0 + 52) lies at or above digit D - 1:
+// the first term anchors it (top bit in the last bit of digit D - 2), a later
+// one moves it up by whole digits.  Returns the new base.
 template <int D, int T>
-__device__ __forceinline__ void fas_add(FixAccS<D, T>& a, double v, bool neg) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const int ef = (int)((bits >> 52) & 0x7ff);
-  unsigned long long m = bits & 0xfffffffffffffULL;
-  if (ef == 0x7ff) {
-    a.bad = true;
-    return;
-  }
-  if (ef) m |= 1ULL << 52;
-  if (m == 0) return;
-  const int e0 = (ef ? ef : 1) - 1075;
-  if (!a.live) {
-    a.base = e0 + 52 - (32 * (D - 1) - 1);
-    a.live = true;
-  }
-  int pos = e0 - a.base;
+__device__ __noinline__ int fas_window(unsigned long long* dp, unsigned long long* dn, int base, int e0) {
+  if (base == kNotLive) return e0 + 52 - (32 * (D - 1) - 1);
+  const int sd = (e0 - base + 52 - (32 * (D - 1) - 1) + 31) >> 5;
+  fas_shift_smem<D, T>(dp, sd);
+  fas_shift_smem<D, T>(dn, sd);
+  return base + 32 * sd;
+}
+
+// a += m 2^e0 (m < 2^53; neg: a -= ...), any e0: the general path, also
+// taken by subnormal terms.  Returns the new base.
+template <int D, int T>
+__device__ __noinline__ int fas_add_general(unsigned long long* dp, unsigned long long* dn, int base,
+                                            unsigned long long m, int e0, bool negative) {
+  if (m == 0) return base;
+  int pos = e0 - base;
   if (pos + 52 >= 32 * (D - 1)) {
-    const int sd = (pos + 52 - (32 * (D - 1) - 1) + 31) >> 5;
-    fas_shift_smem<D, T>(a.dp, sd);
-    fas_shift_smem<D, T>(a.dn, sd);
-    a.base += 32 * sd;
-    pos = e0 - a.base;
+    base = fas_window<D, T>(dp, dn, base, e0);
+    pos = e0 - base;
   }
   if (pos < 0) {
-    if (pos <= -53) return;
+    if (pos <= -53) return base;
     m >>= -pos;
     pos = 0;
   }
   const int w = pos >> 5, r = pos & 31;
   const unsigned long long lo = m << r;
-  const unsigned long long hi = r ? (m >> (64 - r)) : 0ULL;
-  // w + 2 <= D - 1 whenever the top chunk is non-zero (the top bit lies below digit D - 1)
-  unsigned long long* p = (((bits >> 63) != 0) != neg ? a.dn : a.dp) + w * T;
+  const unsigned long long hi = (m >> 1) >> (63 - r);
+  unsigned long long* p = (negative ? dn : dp) + w * T;
   p[0] += lo & 0xffffffffULL;
-  if (w + 1 < D) p[T] += lo >> 32;
-  if (w + 2 < D) p[2 * T] += hi;
+  p[T] += lo >> 32;
+  p[2 * T] += hi;
+  return base;
+}
+
+// a += v (neg: a -= v).  The common case, a normal binary64 term inside the
+// window, takes one test on the exponent field, one on the window and one
+// on the window's lower end; the rest is out of line.  Three digits receive
+// the term's 32-bit chunks: with the top bit below digit D - 1 the third one
+// is at most digit D - 1, so no digit index needs a bounds test.
+template <int D, int T>
+__device__ __forceinline__ void fas_add(FixAccS<D, T>& a, double v, bool neg) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int ef = (int)((bits >> 52) & 0x7ff);
+  const bool negative = ((bits >> 63) != 0) != neg;
+  if ((unsigned)(ef - 1) >= 0x7feu) {  // zero, subnormal, infinity or NaN
+    if (ef == 0x7ff) {
+      a.bad = true;
+    } else if ((bits << 1) != 0) {
+      a.base = fas_add_general<D, T>(a.dp, a.dn, a.base, bits & 0xfffffffffffffULL, -1074, negative);
+    }
+    return;
+  }
+  unsigned long long m = (bits & 0xfffffffffffffULL) | (1ULL << 52);
+  const int e0 = ef - 1075;  // v = +-m 2^e0
+  int pos = e0 - a.base;
+  if (pos > 32 * (D - 1) - 53) {  // first term, or the window has to move up
+    a.base = fas_window<D, T>(a.dp, a.dn, a.base, e0);
+    pos = e0 - a.base;
+  }
+  if (pos < 0) {
+    if (pos <= -53) return;  // entirely below the window
+    m >>= -pos;              // truncate the part below the window
+    pos = 0;
+  }
+  const int w = pos >> 5, r = pos & 31;
+  const unsigned long long lo = m << r;
+  const unsigned long long hi = (m >> 1) >> (63 - r);  // m >> (64 - r), and 0 for r = 0
+  unsigned long long* p = (negative ? a.dn : a.dp) + w * T;
+  p[0] += lo & 0xffffffffULL;
+  p[T] += lo >> 32;
+  p[2 * T] += hi;
 }
 
 // Row flush, kept out of line: it runs once per row and its many temporaries
@@ -295,7 +336,31 @@ __device__ __noinline__ void fas_flush(const unsigned long long* dp, const unsig
 
 template <int L, int D, int T>
 __device__ __forceinline__ void fas_to_mp(const FixAccS<D, T>& a, double* out) {
-  fas_flush<L, D, T>(a.dp, a.dn, a.base, (a.live ? 1 : 0) | (a.bad ? 2 : 0), out);
+  fas_flush<L, D, T>(a.dp, a.dn, a.base, (a.base != kNotLive ? 1 : 0) | (a.bad ? 2 : 0), out);
+}
+
+// ---------------------------------------------------------------------------
+// Sums over many threads: every thread places its terms in register digits at
+// one common base, taken from the largest term of the group (so no term moves
+// the window), and the digits are then added as integers.
+// ---------------------------------------------------------------------------
+// position of the top mantissa bit the accumulator assumes (e0 + 52);
+// INT_MIN for zero and non-finite values
+__device__ __forceinline__ int top_exp(double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int ef = (int)((bits >> 52) & 0x7ff);
+  if (ef == 0x7ff || (bits << 1) == 0) return INT_MIN;
+  return (ef ? ef : 1) - 1075 + 52;
+}
+
+// digits of every thread at the base for block top exponent t
+template <int D>
+__device__ __forceinline__ void fa_at_top(FixAcc<D>& f, int t) {
+  fa_reset<D>(f);
+  if (t != INT_MIN) {
+    f.base = t - (32 * (D - 1) - 1);
+    f.live = true;
+  }
 }
 
 }  // namespace mpk

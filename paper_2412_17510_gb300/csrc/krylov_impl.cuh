@@ -243,15 +243,6 @@ __device__ __forceinline__ void reduce_partials(const double* __restrict__ part,
 // the window (32 (D - 1) - 1 bits under the top), far below u_L relative to
 // it.
 // ---------------------------------------------------------------------------
-// position of the top mantissa bit the accumulator assumes (e0 + 52);
-// INT_MIN for zero and non-finite values
-__device__ __forceinline__ int top_exp(double v) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const int ef = (int)((bits >> 52) & 0x7ff);
-  if (ef == 0x7ff || (bits << 1) == 0) return INT_MIN;
-  return (ef ? ef : 1) - 1075 + 52;
-}
-
 template <int TB>
 __device__ __forceinline__ int block_max_int(int v) {
   __shared__ int s[TB / 32];
@@ -264,16 +255,6 @@ __device__ __forceinline__ int block_max_int(int v) {
   for (int w = 1; w < TB / 32; w++) v = max(v, s[w]);
   __syncthreads();
   return v;
-}
-
-// digits of every thread at the base for block top exponent t
-template <int D>
-__device__ __forceinline__ void fa_at_top(FixAcc<D>& f, int t) {
-  fa_reset<D>(f);
-  if (t != INT_MIN) {
-    f.base = t - (32 * (D - 1) - 1);
-    f.live = true;
-  }
 }
 
 // Sum the digit arrays f[a] over the block; thread 0 gets the totals cut to

@@ -16,12 +16,12 @@ mps = pytest.importorskip("paper_2412_17510_gb300")
 torch = pytest.importorskip("torch")
 
 
-def make_batch(L, count=10, seed=0, nmax=3000, ks=None, kappa=(1e-3, 1e3)):
+def make_batch(L, count=10, seed=0, nmax=3000, ks=None, kappa=(1e-3, 1e3), flags=0):
     specs = workloads.batch_specs(count, n_range=(150, nmax), k_range=(1, 9), seed=seed)
     mats, coos, kk = [], [], []
     for i, (nx, ny, nz, k, sd) in enumerate(specs):
         coo = workloads.diffusion_7pt(nx, ny, nz, kappa_range=kappa, seed=sd)
-        h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, 0, val_limbs=1)
+        h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, flags, val_limbs=1)
         mats.append(h)
         coos.append(coo)
         kk.append(ks[i] if ks else k)
@@ -122,6 +122,47 @@ def test_batch_cg_maxit_and_invalid():
                 mps.mpspmv_batch_create([mats[0], h4], [1, 1], 0)   # mixed precisions
         finally:
             mps.mpspmv_destroy(h4)
+    finally:
+        for h in mats:
+            mps.mpspmv_destroy(h)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_batch_cg_exact_accumulation(L):
+    """Batches of MPSPMV_EXACT_ACC handles: exact products and exact vector
+    kernels.  Every system converges with about the iteration count of the
+    single-handle exact CG and of the oracle's CG, to the target."""
+    mats, coos, ks = make_batch(L, count=5, seed=13, nmax=2500, kappa=(0.1, 10.0), flags=16)
+    rtol = {2: 1e-25, 4: 1e-50}[L]
+    try:
+        b = mps.mpspmv_batch_create(mats, ks, 0)
+        try:
+            Bs = [to_dev(rhs_block(c.ncols, k, L, 300 + 10 * i)) for i, (c, k) in enumerate(zip(coos, ks))]
+            Xs = [torch.zeros_like(B) for B in Bs]
+            st, it, rr, ss = mps.mpspmv_batch_cg(b, Bs, Xs, sum(ks), rtol, 0.0, 20000)
+            assert st == mps.MPSPMV_OK and (ss == 0).all()
+            assert (rr <= 50 * rtol).all()
+            q = 0
+            for i, (h, c, k) in enumerate(zip(mats, coos, ks)):
+                Bh = Bs[i].cpu().numpy()
+                bcol = to_dev(Bh[:, :, 0])
+                xcol = torch.zeros_like(bcol)
+                st1, it1, rr1 = mps.mpspmv_cg(h, bcol, xcol, rtol, 0.0, 20000)
+                assert st1 == 0 and abs(it[q] - it1) <= max(3, 0.05 * it1), (i, it[q], it1)
+                A = oracle.coo_to_csr(c.nrows, c.ncols, c.row, c.col, c.promoted(L), L)
+                ost, ox, oit, orr = oracle.cg(A, Bh[:, :, 0], rtol=rtol, maxit=20000)
+                assert ost == 0 and abs(it[q] - oit) <= max(3, 0.05 * oit)
+                # the batched solution of this system solves it to the target (exact residual)
+                x = Xs[i].cpu().numpy()[:, :, 0]
+                ex_re, _, _, _ = exact.exact_rows(A, x)
+                from fractions import Fraction as F
+                den = 1 << (2 * exact.SCALE)
+                num = sum((exact.to_fraction(Bh[:, j, 0]) - F(ex_re[j], den)) ** 2 for j in range(c.nrows))
+                bb = sum(exact.to_fraction(Bh[:, j, 0]) ** 2 for j in range(c.nrows))
+                assert float(num / bb) ** 0.5 <= 50 * rtol
+                q += k
+        finally:
+            mps.mpspmv_batch_destroy(b)
     finally:
         for h in mats:
             mps.mpspmv_destroy(h)

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kBT) batch_runs_kernel(const BatchEntry* __res
 }
 
 // One thread per (split row, right-hand side) of every matrix.
-template <int L>
+template <int L, bool EXACT>
 __global__ void __launch_bounds__(kBT) batch_combine_kernel(const BatchEntry* __restrict__ E,
                                                             const int64_t* __restrict__ cstart, int nm,
                                                             int64_t total, const int* __restrict__ sys_status) {
@@ -116,6 +116,12 @@ __global__ void __launch_bounds__(kBT) batch_combine_kernel(const BatchEntry* __
   const int64_t c0 = __ldg(m.indptr + r) / m.K;
   const int64_t c1 = (__ldg(m.indptr + r + 1) - 1) / m.K;
   const int kc = be->kc;
+  if (EXACT) {  // the same bits as the single-matrix combine kernels
+    const mp<L> a = combine_exact<L>(be->carry, m.nchunks, kc, rhs, L, 0, c0, c1);
+#pragma unroll
+    for (int l = 0; l < L; l++) be->Y[(int64_t)l * m.nrows * be->ldy + r * be->ldy + rhs] = a.v[l];
+    return;
+  }
   mp<L> acc;
 #pragma unroll
   for (int l = 0; l < L; l++) acc.v[l] = be->carry[((int64_t)(L + l) * m.nchunks + c0) * kc + rhs];
@@ -633,8 +639,13 @@ int enqueue_spmm(mpspmv_batch* b, const int* sys_status, cudaStream_t s) {
                                                                     b->total_items, b->d_head, sys_status);
   MPS_CUDA(cudaGetLastError());
   if (b->total_comb > 0) {
-    batch_combine_kernel<L><<<(unsigned)((b->total_comb + kBT - 1) / kBT), kBT, 0, s>>>(
-        b->d_entries, b->d_comb_start, b->count, b->total_comb, sys_status);
+    const unsigned nb = (unsigned)((b->total_comb + kBT - 1) / kBT);
+    if (b->mats[0]->exact)
+      batch_combine_kernel<L, true><<<nb, kBT, 0, s>>>(b->d_entries, b->d_comb_start, b->count, b->total_comb,
+                                                       sys_status);
+    else
+      batch_combine_kernel<L, false><<<nb, kBT, 0, s>>>(b->d_entries, b->d_comb_start, b->count, b->total_comb,
+                                                        sys_status);
     MPS_CUDA(cudaGetLastError());
   }
   return MPSPMV_OK;

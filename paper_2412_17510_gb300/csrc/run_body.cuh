@@ -252,4 +252,69 @@ __device__ __forceinline__ void process_run_exact(const DevMat& m, int64_t c, in
   }
 }
 
+// Exact sum of the run partials of a row cut by run boundaries (exact-
+// accumulation handles): the starting run's partial (slot 1 of run c0) and
+// the partials of runs c0+1 .. c1 (slot 0), components off .. off+L-1 of the
+// carry buffer.  All components go into register digits at the base of the
+// largest one and are cut to L components once.  The result depends only on
+// the set of components, so every kernel that combines a row this way (one
+// thread or one warp per row) gives the same bits.
+template <int L>
+__device__ __forceinline__ mp<L> combine_exact(const double* __restrict__ carry, int64_t nchunks, int kc, int rhs,
+                                               int P, int off, int64_t c0, int64_t c1) {
+  constexpr int D = AccDigits<L>::D;
+  auto ld = [&](int w, int l, int64_t c) { return carry[((int64_t)(w * P + off + l) * nchunks + c) * kc + rhs]; };
+  int t = INT_MIN;
+#pragma unroll
+  for (int l = 0; l < L; l++) t = max(t, top_exp(ld(1, l, c0)));
+  for (int64_t c = c0 + 1; c <= c1; c++)
+#pragma unroll
+    for (int l = 0; l < L; l++) t = max(t, top_exp(ld(0, l, c)));
+  FixAcc<D> f;
+  fa_at_top<D>(f, t);
+#pragma unroll
+  for (int l = 0; l < L; l++) fa_add<D>(f, ld(1, l, c0));
+  for (int64_t c = c0 + 1; c <= c1; c++)
+#pragma unroll
+    for (int l = 0; l < L; l++) fa_add<D>(f, ld(0, l, c));
+  mp<L> r;
+  fa_to_mp<L, D>(f, r.v);
+  return r;
+}
+
+// The same sum by one warp: lane j takes runs c0+1+j, c0+1+j+32, ... (lane 0
+// also the starting partial); the base comes from a warp-wide maximum and
+// the digits are added by integer shuffles.  Valid in lane 0.
+template <int L>
+__device__ __forceinline__ mp<L> combine_exact_warp(const double* __restrict__ carry, int64_t nchunks, int kc,
+                                                    int rhs, int P, int off, int64_t c0, int64_t c1, int lane) {
+  constexpr int D = AccDigits<L>::D;
+  auto ld = [&](int w, int l, int64_t c) { return carry[((int64_t)(w * P + off + l) * nchunks + c) * kc + rhs]; };
+  int t = INT_MIN;
+  if (lane == 0)
+#pragma unroll
+    for (int l = 0; l < L; l++) t = max(t, top_exp(ld(1, l, c0)));
+  for (int64_t c = c0 + 1 + lane; c <= c1; c += 32)
+#pragma unroll
+    for (int l = 0; l < L; l++) t = max(t, top_exp(ld(0, l, c)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+  FixAcc<D> f;
+  fa_at_top<D>(f, t);
+  if (lane == 0)
+#pragma unroll
+    for (int l = 0; l < L; l++) fa_add<D>(f, ld(1, l, c0));
+  for (int64_t c = c0 + 1 + lane; c <= c1; c += 32)
+#pragma unroll
+    for (int l = 0; l < L; l++) fa_add<D>(f, ld(0, l, c));
+  f.bad = __any_sync(0xffffffffu, f.bad);
+#pragma unroll
+  for (int j = 0; j < D; j++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f.d[j] += __shfl_down_sync(0xffffffffu, f.d[j], o);
+  mp<L> r;
+  fa_to_mp<L, D>(f, r.v);
+  return r;
+}
+
 }  // namespace mpk

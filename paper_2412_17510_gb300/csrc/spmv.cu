@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, EXACT ? (CPLX ? 3 : (L >= 3 ? 6 : 5)
 // Rows cut by run boundaries: partial of the run where the row starts (slot
 // w = 1), then the partials of the following runs (slot w = 0) in order.
 // One thread per (row, right-hand side) for rows spanning few runs.
-template <int L, bool CPLX>
+template <int L, bool CPLX, bool EXACT>
 __global__ void __launch_bounds__(kThreads) combine_kernel(DevMat m, double* __restrict__ y, int64_t ys,
                                                            int64_t yoff, const double* __restrict__ carry,
                                                            int kc, int k, const int* __restrict__ gate) {
@@ -106,6 +106,12 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(DevMat m, double* __r
   const int64_t r = __ldg(m.split_rows + s);
   const int64_t c0 = __ldg(m.indptr + r) / m.K;
   const int64_t c1 = (__ldg(m.indptr + r + 1) - 1) / m.K;
+  if (EXACT) {
+    const mp<L> er = combine_exact<L>(carry, m.nchunks, kc, rhs, P, 0, c0, c1);
+    const mp<L> ei = CPLX ? combine_exact<L>(carry, m.nchunks, kc, rhs, P, L, c0, c1) : mp_zero<L>();
+    store_mp<L, CPLX>(y + rhs, ys, r * yoff, er, ei);
+    return;
+  }
   auto ld = [&](int w, int p, int64_t c) { return carry[((int64_t)(w * P + p) * m.nchunks + c) * kc + rhs]; };
   mp<L> sr, si;
 #pragma unroll
@@ -140,7 +146,7 @@ __device__ __forceinline__ mp<L> shfl_down_mp(const mp<L>& a, int off) {
 // side).  Lane l sums the following-run partials c0+1+l, c0+1+l+32, ... in
 // order, a shuffle tree adds the 32 lane sums, and the starting run's partial
 // goes in front.
-template <int L, bool CPLX>
+template <int L, bool CPLX, bool EXACT>
 __global__ void __launch_bounds__(kThreads) combine_long_kernel(DevMat m, double* __restrict__ y, int64_t ys,
                                                                 int64_t yoff, const double* __restrict__ carry,
                                                                 int kc, int k, const int* __restrict__ gate) {
@@ -154,6 +160,12 @@ __global__ void __launch_bounds__(kThreads) combine_long_kernel(DevMat m, double
   const int64_t r = __ldg(m.split_rows + m.nshort + s);
   const int64_t c0 = __ldg(m.indptr + r) / m.K;
   const int64_t c1 = (__ldg(m.indptr + r + 1) - 1) / m.K;
+  if (EXACT) {
+    const mp<L> er = combine_exact_warp<L>(carry, m.nchunks, kc, rhs, P, 0, c0, c1, lane);
+    const mp<L> ei = CPLX ? combine_exact_warp<L>(carry, m.nchunks, kc, rhs, P, L, c0, c1, lane) : mp_zero<L>();
+    if (lane == 0) store_mp<L, CPLX>(y + rhs, ys, r * yoff, er, ei);
+    return;
+  }
   auto ld = [&](int w, int p, int64_t c) { return carry[((int64_t)(w * P + p) * m.nchunks + c) * kc + rhs]; };
   mp<L> sr = mp_zero<L>(), si = mp_zero<L>();
   for (int64_t c = c0 + 1 + lane; c <= c1; c += 32) {
@@ -234,14 +246,20 @@ int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, d
   MPS_CUDA(cudaGetLastError());
   if (h->nshort > 0) {
     const int64_t ct = h->nshort * k;
-    combine_kernel<L, CPLX><<<(unsigned)((ct + kThreads - 1) / kThreads), kThreads, 0, s>>>(m, y, ys, yoff, h->d_carry,
-                                                                                         h->carry_k, k, gate);
+    const unsigned nb = (unsigned)((ct + kThreads - 1) / kThreads);
+    if (h->exact)
+      combine_kernel<L, CPLX, true><<<nb, kThreads, 0, s>>>(m, y, ys, yoff, h->d_carry, h->carry_k, k, gate);
+    else
+      combine_kernel<L, CPLX, false><<<nb, kThreads, 0, s>>>(m, y, ys, yoff, h->d_carry, h->carry_k, k, gate);
     MPS_CUDA(cudaGetLastError());
   }
   if (h->nsplit > h->nshort) {
     const int64_t ct = (h->nsplit - h->nshort) * k * 32;
-    combine_long_kernel<L, CPLX><<<(unsigned)((ct + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-        m, y, ys, yoff, h->d_carry, h->carry_k, k, gate);
+    const unsigned nb = (unsigned)((ct + kThreads - 1) / kThreads);
+    if (h->exact)
+      combine_long_kernel<L, CPLX, true><<<nb, kThreads, 0, s>>>(m, y, ys, yoff, h->d_carry, h->carry_k, k, gate);
+    else
+      combine_long_kernel<L, CPLX, false><<<nb, kThreads, 0, s>>>(m, y, ys, yoff, h->d_carry, h->carry_k, k, gate);
     MPS_CUDA(cudaGetLastError());
   }
   return MPSPMV_OK;

@@ -205,12 +205,6 @@ def run_reference(args):
     import multiprocessing as mp
     ncores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
-    if args.cg_only:
-        # profiling entry: one CG variant, no timed SpMV step
-        out = suite_cg(mps, torch.cuda.current_stream(), args.small, only=args.cg_only, its=args.cg_iters)
-        print(json.dumps(out))
-        return
-
     mats = make_matrices(args.small)
     xs = {m: {L: workloads.full_limb_vector(c.ncols, L, seed=0) for L in PRECS} for m, c in mats.items()}
     nnz_of = {(m, L): c.nnz for m, c in mats.items() for L in PRECS}
@@ -503,7 +497,7 @@ def main():
     pool = None
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if rank == 0 and world == 1 and not args.no_cpu and not args.only:
+    if rank == 0 and world == 1 and not args.no_cpu and not args.only and not args.cg_only:
         # spawn the oracle workers before the first GPU call
         pool = mp.get_context("spawn").Pool(ncores)
 
@@ -515,6 +509,12 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    if args.cg_only:
+        # profiling entry: one CG variant, no timed SpMV step
+        out = suite_cg(mps, torch.cuda.current_stream(), args.small, only=args.cg_only, its=args.cg_iters)
+        print(json.dumps(out))
+        return
 
     mats = make_matrices(args.small)
     ariths = ["exact", "paper"] if args.arith == "both" else [args.arith]

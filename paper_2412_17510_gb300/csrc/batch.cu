@@ -28,7 +28,12 @@ using namespace mpk;
 namespace {
 
 constexpr int kBT = 256;  // threads per block (run kernel and vector kernels)
-constexpr int kRB = 2048; // rows per vector block in the batched Krylov kernels
+// Rows per vector block of the batched Krylov kernels: the paper-order
+// kernels use long blocks; the exact ones do more integer work per element
+// in 128-thread blocks, and the small systems of a batch then need shorter
+// blocks to fill the GPU.
+constexpr int kRB = 2048;
+constexpr int kRBX = 512;
 constexpr int kCgItersPerGraph = 8;
 
 struct BatchEntry {
@@ -42,6 +47,7 @@ struct BatchEntry {
   int64_t ldy;
   int64_t sys0;  // first system index (batched CG)
   int64_t vb0;   // first vector block (batched CG)
+  int64_t rb;    // rows per vector block (batched CG)
 };
 
 struct CgSys {  // per-system solver state (structure of arrays)
@@ -141,7 +147,7 @@ __global__ void fill_kernel(double* p, int64_t n, double seed) {
 }
 
 // ---------------------------------------------------------------------------
-// batched CG vector kernels: block = (matrix, kRB rows), thread = (row
+// batched CG vector kernels: block = (matrix, rb rows), thread = (row
 // stripe, right-hand side); right-hand sides are contiguous in the n x ld
 // row-major planes.
 // ---------------------------------------------------------------------------
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kBT) batch_vec_kernel(const BatchEntry* __rest
   const int kp = be->kp, k = be->k;
   const int64_t n = be->m.nrows, ld = be->ldx;
   const int64_t plane = n * ld;
-  const int64_t r0 = (vb - __ldg(vstart + e)) * kRB;
+  const int64_t r0 = (vb - __ldg(vstart + e)) * be->rb;
   const int rhs = threadIdx.x & (kp - 1);
   const int stripe = threadIdx.x / kp, nstripe = kBT / kp;
   const int64_t sys = be->sys0 + rhs;
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(kBT) batch_vec_kernel(const BatchEntry* __rest
   }
   if (live && OP == V_P) be_ = lds<L>(S.beta, sys);
   if (live) {
-    const int64_t rend = min(r0 + kRB, n);
+    const int64_t rend = min(r0 + be->rb, n);
     for (int64_t r = r0 + stripe; r < rend; r += nstripe) {
       const int64_t idx = r * ld + rhs;
       if (OP == V_RESID) {  // v0 = b, v1 = q (A x), v2 = r, v3 = p
@@ -385,7 +391,7 @@ __global__ void __launch_bounds__(kBTX) batch_vec_kernel_x(const BatchEntry* __r
   const int kp = be->kp, k = be->k;
   const int64_t n = be->m.nrows, ld = be->ldx;
   const int64_t plane = n * ld;
-  const int64_t r0 = (vb - __ldg(vstart + e)) * kRB;
+  const int64_t r0 = (vb - __ldg(vstart + e)) * be->rb;
   const int rhs = threadIdx.x & (kp - 1);
   const int stripe = threadIdx.x / kp, nstripe = kBTX / kp;
   const int64_t sys = be->sys0 + rhs;
@@ -403,7 +409,7 @@ __global__ void __launch_bounds__(kBTX) batch_vec_kernel_x(const BatchEntry* __r
   if (live && OP == V_XR) al = lds<L>(S.alpha, sys);
   if (live && OP == V_P) be_ = lds<L>(S.beta, sys);
   if (live) {
-    const int64_t rend = min(r0 + kRB, n);
+    const int64_t rend = min(r0 + be->rb, n);
     for (int64_t r = r0 + stripe; r < rend; r += nstripe) {
       const int64_t idx = r * ld + rhs;
       if (OP == V_RESID) {  // v0 = b, v1 = q (A x), v2 = r, v3 = p
@@ -470,7 +476,7 @@ __global__ void batch_finish_kernel(const BatchEntry* __restrict__ E, const int6
   const int e = find_entry(sstart, nm, sys);
   const BatchEntry* be = E + e;
   const int rhs = (int)(sys - be->sys0);
-  const int64_t nb = (be->m.nrows + kRB - 1) / kRB;
+  const int64_t nb = (be->m.nrows + be->rb - 1) / be->rb;
   mp<L> a = mp_zero<L>(), b = mp_zero<L>();
   if (EX) {
     a = sum_partials_x<L>(part, be->vb0, nb, rhs);
@@ -590,7 +596,8 @@ int layout(mpspmv_batch* b, cudaStream_t s) {
     b->item_start[i + 1] = b->item_start[i] + groups * ((k + w - 1) / w);
     b->comb_start[i + 1] = b->comb_start[i] + h->nsplit * k;
     b->sys_start[i + 1] = b->sys_start[i] + k;
-    b->vec_start[i + 1] = b->vec_start[i] + (h->nrows + kRB - 1) / kRB;
+    const int64_t rb = h->exact ? kRBX : kRB;
+    b->vec_start[i + 1] = b->vec_start[i] + (h->nrows + rb - 1) / rb;
     BatchEntry& e = b->h_entries[i];
     e.m = h->view();
     e.carry = h->d_carry;
@@ -603,6 +610,7 @@ int layout(mpspmv_batch* b, cudaStream_t s) {
     e.ldx = e.ldy = k;
     e.sys0 = b->sys_start[i];
     e.vb0 = b->vec_start[i];
+    e.rb = rb;
   }
   b->total_items = b->item_start[n];
   b->total_comb = b->comb_start[n];

@@ -203,20 +203,16 @@ __device__ __forceinline__ void process_run_exact(const DevMat& m, int64_t c, in
   bool have = false;
   const int n = (int)(k1 - k0);
   const int64_t chunk_base = tile_pos(c, 0, m.K);
-  // software pipeline: column indices two entries ahead, values and x one
-  // entry ahead, so the gathers overlap the integer work of the current entry
-  EntryIn<L, CPLX, MIXED> cur, nxt;
-  int64_t col1 = 0;
-  if (n > 0) load_entry<L, CPLX, MIXED>(m, chunk_base, __ldg(m.cols + chunk_base), xr, xs, xoff, cur);
-  if (n > 1) col1 = __ldg(m.cols + chunk_base + 32);
+  // Entries are loaded in the step that uses them: the resident warps (6 to
+  // 8 blocks of 128 threads) hide the gathers' latency, and holding the next
+  // entry's operands in registers cost more (spills, fewer blocks) than it
+  // saved.
 #pragma unroll 1
   for (int j = 0; j < n; j++) {
-    int64_t col2 = 0;
-    if (j + 1 < n) load_entry<L, CPLX, MIXED>(m, chunk_base + (int64_t)(j + 1) * 32, col1, xr, xs, xoff, nxt);
-    if (j + 2 < n) col2 = __ldg(m.cols + chunk_base + (int64_t)(j + 2) * 32);
+    EntryIn<L, CPLX, MIXED> cur;
+    const int64_t pos = chunk_base + (int64_t)j * 32;
+    load_entry<L, CPLX, MIXED>(m, pos, __ldg(m.cols + pos), xr, xs, xoff, cur);
     compute_entry<L, CPLX, MIXED>(cur, sr, si);
-    cur = nxt;
-    col1 = col2;
     have = true;
     const int64_t kk = k0 + j + 1;
     if (kk == rend) {

@@ -72,12 +72,18 @@ __global__ void build_tiles_kernel(DevMat m, int32_t* __restrict__ cols_out, dou
 // Carry layout: carry[((w*P + p)*nchunks + c)*kc + rhs], w = 0 first-row
 // partial, w = 1 last-row partial.
 // The exact variant is bound by integer issue and latency, so it asks for
-// more resident blocks (fewer registers): measured on the stencil and
-// power-law steps, 5 blocks suit DD and 6 suit TD/QD; the complex variant's
-// shared memory allows only 5 blocks and more register pressure spills.
+// more resident blocks (fewer registers): timed on the stencil and
+// power-law steps over 5..8 blocks, DD runs best with 7, TD with 8 and QD
+// with 6; the complex variant's shared memory allows only 5 blocks and more
+// register pressure spills.
 // ---------------------------------------------------------------------------
+template <int L>
+constexpr int exact_min_blocks() {
+  return L == 3 ? 8 : (L == 4 ? 6 : 7);
+}
+
 template <int L, bool CPLX, bool MIXED, bool EXACT>
-__global__ void __launch_bounds__(kThreads, EXACT ? (CPLX ? 3 : (L >= 3 ? 6 : 5)) : 1) spmv_runs_kernel(DevMat m, const double* __restrict__ x, int64_t xs,
+__global__ void __launch_bounds__(kThreads, EXACT ? (CPLX ? 3 : exact_min_blocks<L>()) : 1) spmv_runs_kernel(DevMat m, const double* __restrict__ x, int64_t xs,
                                                              int64_t xoff, double* __restrict__ y, int64_t ys,
                                                              int64_t yoff, double* __restrict__ carry, int kc,
                                                              int kp, int k, const int* __restrict__ gate) {

@@ -320,18 +320,68 @@ __device__ __forceinline__ void fas_add(FixAccS<D, T>& a, double v, bool neg) {
 }
 
 // Row flush, kept out of line: it runs once per row and its many temporaries
-// would otherwise raise the register count of the whole per-entry loop.
+// would otherwise raise the register count of the whole per-entry loop.  In
+// a warp the rows of different threads end at different steps, so the flush
+// mostly runs in a divergent branch: it is kept short.  One signed carry pass
+// leaves 32-bit magnitude digits in dp (dn is left as it is; callers reset
+// the accumulator afterwards), a negative sum is negated in two's complement,
+// and each component's 53 bits come from three digits read at a computed
+// index, cut by truncation.
 template <int L, int D, int T>
-__device__ __noinline__ void fas_flush(const unsigned long long* dp, const unsigned long long* dn, int base,
-                                       int flags, double* out) {
-  FixAcc<D> r;
-  // each array's digits are below 2^63, so their difference fits a signed digit
+__device__ __noinline__ void fas_flush(unsigned long long* dp, const unsigned long long* dn, int base, int flags,
+                                       double* out) {
 #pragma unroll
-  for (int j = 0; j < D; j++) r.d[j] = (long long)dp[j * T] - (long long)dn[j * T];
-  r.base = base;
-  r.live = flags & 1;
-  r.bad = (flags & 2) != 0;
-  fa_to_mp<L, D>(r, out);
+  for (int l = 0; l < L; l++) out[l] = 0.0;
+  if (flags & 2) {
+    out[0] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
+  if (!(flags & 1)) return;
+  // value = sum_j (dp_j - dn_j) 2^(32 j); every digit is below 2^63
+  long long c = 0;
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    const long long v = (long long)dp[j * T] - (long long)dn[j * T] + c;
+    c = v >> 32;  // floor(v / 2^32)
+    dp[j * T] = (unsigned long long)(v & 0xffffffffLL);
+  }
+  // value = sum_j dp_j 2^(32 j) + c 2^(32 D); the head-room digit keeps
+  // |value| below 2^(32 D), so c is 0 or -1
+  const bool neg = c < 0;
+  if (neg) {  // magnitude = (2^(32 D) - sum) in two's complement over D digits
+    unsigned long long carry = 1;
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+      const unsigned long long t = (unsigned long long)(~(unsigned int)dp[j * T]) + carry;
+      dp[j * T] = t & 0xffffffffULL;
+      carry = t >> 32;
+    }
+  }
+  int top = -1;
+  for (int j = D - 1; j >= 0; j--) {
+    const unsigned int dj = (unsigned int)dp[j * T];
+    if (dj) {
+      top = 32 * j + 31 - __clz(dj);
+      break;
+    }
+  }
+  if (top < 0) return;
+  constexpr unsigned long long kMask = (1ULL << 53) - 1;
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    const int lsb = top - 52 - 53 * l;  // component l holds bits lsb .. lsb + 52
+    if (lsb + 52 < 0) break;
+    unsigned long long chunk;
+    if (lsb >= 0) {
+      const int w = lsb >> 5, r = lsb & 31;  // w + 1 <= D - 1 since lsb + 52 <= top < 32 D
+      const unsigned long long lo = dp[w * T] | (dp[(w + 1) * T] << 32);
+      const unsigned long long hi = (w + 2 < D) ? dp[(w + 2) * T] : 0ULL;
+      chunk = ((lo >> r) | ((hi << 1) << (63 - r))) & kMask;  // hi << (64 - r), and 0 for r = 0
+    } else {
+      chunk = ((dp[0] | (dp[T] << 32)) << (-lsb)) & kMask;
+    }
+    out[l] = chunk_to_double(chunk, lsb + base, neg);
+  }
 }
 
 template <int L, int D, int T>

@@ -39,6 +39,7 @@ void free_handle(mpspmv_mat* h) {
   cudaFree(h->d_chunk_row);
   cudaFree(h->d_split);
   cudaFree(h->d_carry);
+  cudaFree(h->d_xint);
   cudaFree(h->d_xbuf);
   cudaFree(h->d_ybuf);
   cudaFree(h->d_kws);
@@ -247,6 +248,7 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
     TRY(dev_alloc(h, &h->d_vals, (int64_t)h->Pv * tlen));
     TRY(dev_alloc(h, &h->d_chunk_row, nchunks));
     TRY(dev_alloc(h, &h->d_split, h->nsplit));
+    if (h->exact && h->P > 1) TRY(dev_alloc(h, &h->d_xint, (int64_t)h->P * ncols));
     TRY(mps_ensure_carry(h, 1));
     if (cudaMemcpyAsync(h->d_indptr, indptr.data(), sizeof(int64_t) * (nrows + 1), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||

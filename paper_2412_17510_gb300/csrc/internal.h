@@ -60,6 +60,7 @@ struct mpspmv_mat {
   int64_t* d_split = nullptr;
   double* d_carry = nullptr;      // 2 * P * nchunks * carry_k
   int carry_k = 0;                // right-hand sides the carry buffer holds
+  double* d_xint = nullptr;       // exact handles: x with the P components of a column adjacent
   double* d_xbuf = nullptr;       // host-buffer entry points
   double* d_ybuf = nullptr;
   double* d_kws = nullptr;        // Krylov vectors and reduction partials

@@ -208,6 +208,19 @@ __global__ void __launch_bounds__(kThreads) combine_long_kernel(DevMat m, double
   }
 }
 
+// xi[col * P + p] = x[p * n + col]: the components of one column adjacent,
+// so an exact run kernel gathers them from one 32-byte sector (real QD)
+// instead of P sectors of P planes.  Gated like the run kernel.
+__global__ void interleave_kernel(const double* __restrict__ x, int64_t n, int P, double* __restrict__ xi,
+                                  const int* gate) {
+  if (gate && *gate != 0) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * P) return;
+  const int64_t col = t / P;
+  const int p = (int)(t - col * P);
+  xi[t] = x[(int64_t)p * n + col];
+}
+
 // y = 0 (single right-hand side), gated
 __global__ void zero_kernel(double* y, int64_t ys, int64_t yoff, int64_t nrows, int P, const int* gate) {
   if (gate && *gate != 0) return;
@@ -241,6 +254,15 @@ int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, d
   }
   int kp = 1;
   while (kp < k) kp <<= 1;
+  if (h->exact && k == 1 && h->d_xint) {  // single vector: gather from the interleaved copy
+    const int64_t tot = (int64_t)h->P * h->ncols;
+    interleave_kernel<<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(x, h->ncols, h->P, h->d_xint,
+                                                                                     gate);
+    MPS_CUDA(cudaGetLastError());
+    x = h->d_xint;
+    xs = 1;
+    xoff = h->P;
+  }
   const int64_t threads = h->nchunks * kp;
   const int64_t blocks = (threads + kThreads - 1) / kThreads;
   if (h->exact)

@@ -40,6 +40,9 @@ void free_handle(mpspmv_mat* h) {
   cudaFree(h->d_split);
   cudaFree(h->d_carry);
   cudaFree(h->d_xint);
+  cudaFree(h->d_slice_ptr);
+  cudaFree(h->d_sell_cols);
+  cudaFree(h->d_sell_vals);
   cudaFree(h->d_xbuf);
   cudaFree(h->d_ybuf);
   cudaFree(h->d_kws);
@@ -296,6 +299,7 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
         }
       }
       TRY(mps_build_tiles(h, d_vin, nin, (mixed || h->dstore) ? 1 : val_limbs, d_runs, d_col, s));
+      if (h->exact) TRY(mps_build_sell(h, s));
       if (cudaStreamSynchronize(s) != cudaSuccess) {
         st = MPSPMV_ECUDA;
         goto fail;

@@ -61,6 +61,13 @@ struct mpspmv_mat {
   double* d_carry = nullptr;      // 2 * P * nchunks * carry_k
   int carry_k = 0;                // right-hand sides the carry buffer holds
   double* d_xint = nullptr;       // exact handles: x with the P components of a column adjacent
+  // Exact handles with short, evenly sized rows: a sliced-ELL copy for
+  // single-vector products (slices of 32 rows, entry q of row r at
+  // slice_ptr[r / 32] + 32 q + r % 32), one thread per row.
+  int64_t sell_len = 0;           // slots per value plane (0: no copy)
+  int64_t* d_slice_ptr = nullptr; // nrows / 32 + 1 slice offsets
+  int32_t* d_sell_cols = nullptr;
+  double* d_sell_vals = nullptr;  // Pv planes of sell_len
   double* d_xbuf = nullptr;       // host-buffer entry points
   double* d_ybuf = nullptr;
   double* d_kws = nullptr;        // Krylov vectors and reduction partials
@@ -82,6 +89,9 @@ struct mpspmv_mat {
 // Launchers implemented in spmv.cu
 int mps_build_tiles(mpspmv_mat* h, const double* d_sorted_vals, int64_t nin, int vin_limbs,
                     const int64_t* d_run_start, const int64_t* d_unique_cols_src, cudaStream_t s);
+// Sliced-ELL copy of a built matrix (exact handles with short, evenly sized
+// rows); no-op when the rows do not qualify.
+int mps_build_sell(mpspmv_mat* h, cudaStream_t s);
 int mps_launch_spmv(const mpspmv_mat* h, const double* x, double* y, cudaStream_t s);
 // SpMV whose kernels do nothing unless *gate == 0 (device flag, e.g. the
 // status word of a Krylov solver replayed from a CUDA graph).

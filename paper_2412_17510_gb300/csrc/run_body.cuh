@@ -248,6 +248,38 @@ __device__ __forceinline__ void process_run_exact(const DevMat& m, int64_t c, in
   }
 }
 
+// One whole row per thread from the sliced-ELL copy (exact accumulation):
+// entry q of row r at base + 32 q + r % 32, so the 32 threads of a warp read
+// 32 consecutive slots per step, and all of them flush at the end of the
+// loop instead of whenever one of their rows ends.  T is the block size.
+template <int L, bool CPLX, bool MIXED, int T>
+__device__ __forceinline__ void process_row_exact(const DevMat& m, int64_t base, int64_t r,
+                                                  const double* __restrict__ x, int64_t xs, int64_t xoff,
+                                                  double* __restrict__ y, int64_t ys, int64_t yoff) {
+  constexpr int D = AccDigits<L>::D;
+  __shared__ unsigned long long s_digits[(CPLX ? 4 : 2) * D * T];
+  FixAccS<D, T> sr, si;
+  sr.dp = s_digits + threadIdx.x;
+  sr.dn = s_digits + D * T + threadIdx.x;
+  si.dp = s_digits + (CPLX ? 2 * D * T : 0) + threadIdx.x;
+  si.dn = s_digits + (CPLX ? 3 * D * T : D * T) + threadIdx.x;
+  fas_reset<D, T>(sr);
+  if (CPLX) fas_reset<D, T>(si);
+  const int64_t len = __ldg(m.indptr + r + 1) - __ldg(m.indptr + r);
+  const int64_t slot0 = base + (r & 31);
+#pragma unroll 1
+  for (int64_t q = 0; q < len; q++) {
+    EntryIn<L, CPLX, MIXED> e;
+    const int64_t pos = slot0 + 32 * q;
+    load_entry<L, CPLX, MIXED>(m, pos, __ldg(m.cols + pos), x, xs, xoff, e);
+    compute_entry<L, CPLX, MIXED>(e, sr, si);
+  }
+  mp<L> vr, vi = mp_zero<L>();
+  fas_to_mp<L, D, T>(sr, vr.v);
+  if (CPLX) fas_to_mp<L, D, T>(si, vi.v);
+  store_mp<L, CPLX>(y, ys, r * yoff, vr, vi);
+}
+
 // Exact sum of the run partials of a row cut by run boundaries (exact-
 // accumulation handles): the starting run's partial (slot 1 of run c0) and
 // the partials of runs c0+1 .. c1 (slot 0), components off .. off+L-1 of the

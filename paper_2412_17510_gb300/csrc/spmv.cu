@@ -65,6 +65,38 @@ __global__ void build_tiles_kernel(DevMat m, int32_t* __restrict__ cols_out, dou
   }
 }
 
+// Sliced-ELL copy of the tiled arrays: entry u (CSR order) of row r at
+// offset q goes to slice_ptr[r / 32] + 32 q + r % 32.
+__global__ void build_sell_kernel(DevMat m, const int64_t* __restrict__ slice_ptr, int32_t* __restrict__ cols_out,
+                                  double* __restrict__ vals_out, int64_t sell_len, int Pv) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= m.nnz) return;
+  int64_t lo = 0, hi = m.nrows - 1;  // the row holding entry u: last r with indptr[r] <= u
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(m.indptr + mid) <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t r = lo, q = u - __ldg(m.indptr + r);
+  const int64_t ps = __ldg(slice_ptr + (r >> 5)) + 32 * q + (r & 31);
+  const int64_t c = u / m.K;
+  const int64_t pt = tile_pos(c, (int)(u - c * m.K), m.K);
+  cols_out[ps] = m.cols[pt];
+  for (int p = 0; p < Pv; p++) vals_out[(int64_t)p * sell_len + ps] = m.vals[(int64_t)p * m.tlen + pt];
+}
+
+// One thread per row of the sliced-ELL copy (exact accumulation, single
+// vector); residency as the run kernel's exact variant.
+template <int L, bool CPLX, bool MIXED>
+__global__ void __launch_bounds__(kThreads, CPLX ? 3 : (L == 4 ? 6 : 7))
+    sell_exact_kernel(DevMat m, const int64_t* __restrict__ slice_ptr, const double* __restrict__ x, int64_t xs,
+                      int64_t xoff, double* __restrict__ y, int64_t ys, int64_t yoff, const int* __restrict__ gate) {
+  if (gate && *gate != 0) return;
+  const int64_t r = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (r >= m.nrows) return;
+  process_row_exact<L, CPLX, MIXED, kThreads>(m, __ldg(slice_ptr + (r >> 5)), r, x, xs, xoff, y, ys, yoff);
+}
+
 // ---------------------------------------------------------------------------
 // Run kernel.  Vectors: x plane stride xs, entry j at x[j*xoff] within a plane
 // (xoff = ldx for SpMM, 1 for SpMV); y likewise.  rhs selects the column of a
@@ -263,6 +295,16 @@ int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, d
     xs = 1;
     xoff = h->P;
   }
+  if (h->exact && k == 1 && h->sell_len > 0) {  // short, even rows: whole rows per thread
+    DevMat ms = m;
+    ms.cols = h->d_sell_cols;
+    ms.vals = h->d_sell_vals;
+    ms.tlen = h->sell_len;
+    sell_exact_kernel<L, CPLX, MIXED><<<(unsigned)((h->nrows + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        ms, h->d_slice_ptr, x, xs, xoff, y, ys, yoff, gate);
+    MPS_CUDA(cudaGetLastError());
+    return MPSPMV_OK;
+  }
   const int64_t threads = h->nchunks * kp;
   const int64_t blocks = (threads + kThreads - 1) / kThreads;
   if (h->exact)
@@ -331,6 +373,36 @@ int build_one(mpspmv_mat* h, const double* vin, int64_t nin, int vin_limbs, cons
 int mps_build_tiles(mpspmv_mat* h, const double* d_sorted_vals, int64_t nin, int vin_limbs,
                     const int64_t* d_run_start, const int64_t* d_col_src, cudaStream_t s) {
   MPS_DISPATCH(build_one, h, h, d_sorted_vals, nin, vin_limbs, d_run_start, d_col_src, s);
+}
+
+int mps_build_sell(mpspmv_mat* h, cudaStream_t s) {
+  // rows qualify when short and evenly sized: the slices pad at most 25 %
+  if (h->nnz == 0 || h->max_row_nnz > 128) return MPSPMV_OK;
+  const int64_t nsl = (h->nrows + 31) / 32;
+  std::vector<int64_t> sp(nsl + 1, 0);
+  for (int64_t sl = 0; sl < nsl; sl++) {
+    int64_t w = 0;
+    for (int64_t r = sl * 32; r < std::min<int64_t>(h->nrows, sl * 32 + 32); r++)
+      w = std::max<int64_t>(w, h->h_indptr[r + 1] - h->h_indptr[r]);
+    sp[sl + 1] = sp[sl] + 32 * w;
+  }
+  const int64_t len = sp[nsl];
+  if (len * 4 > h->nnz * 5) return MPSPMV_OK;
+  const size_t bsp = sizeof(int64_t) * (nsl + 1), bc = sizeof(int32_t) * len, bv = sizeof(double) * h->Pv * len;
+  if (cudaMalloc(&h->d_slice_ptr, bsp) != cudaSuccess || cudaMalloc(&h->d_sell_cols, bc) != cudaSuccess ||
+      cudaMalloc(&h->d_sell_vals, bv) != cudaSuccess) {
+    cudaGetLastError();
+    return MPSPMV_ENOMEM;  // the handle's teardown frees what was allocated
+  }
+  h->device_bytes += (int64_t)(bsp + bc + bv);
+  MPS_CUDA(cudaMemcpyAsync(h->d_slice_ptr, sp.data(), bsp, cudaMemcpyHostToDevice, s));
+  MPS_CUDA(cudaMemsetAsync(h->d_sell_cols, 0, bc, s));
+  MPS_CUDA(cudaMemsetAsync(h->d_sell_vals, 0, bv, s));
+  build_sell_kernel<<<(unsigned)((h->nnz + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      h->view(), h->d_slice_ptr, h->d_sell_cols, h->d_sell_vals, len, h->Pv);
+  MPS_CUDA(cudaGetLastError());
+  h->sell_len = len;
+  return MPSPMV_OK;
 }
 
 int mps_ensure_carry(mpspmv_mat* h, int k) {

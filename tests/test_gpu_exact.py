@@ -8,7 +8,7 @@ import pytest
 import oracle
 import workloads
 from oracle import exact
-from tests._util import csr_pair, gpu_spmv, to_dev
+from tests._util import csr_pair, gpu_spmv, to_dev, unsplit_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -167,3 +167,73 @@ def test_binary64_storage_is_bit_identical(L, cplx):
     finally:
         mps.mpspmv_destroy(h1)
         mps.mpspmv_destroy(h2)
+
+
+def _near_uniform(n, ncols, lo, hi, empty_frac, seed, cplx, L):
+    """Rows of lo..hi entries (a few empty): short, evenly sized rows, the
+    kind that gets the one-row-per-thread copy."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(lo, hi + 1, n)
+    lens[rng.random(n) < empty_frac] = 0
+    rows = np.repeat(np.arange(n), lens)
+    cols = np.concatenate([np.sort(rng.choice(ncols, k, replace=False)) for k in lens])
+    P = 2 * L if cplx else L
+    vals = workloads.full_limb_vector(rows.shape[0], L, seed=seed + 1, cplx=cplx)
+    return workloads.COO(n, ncols, rows, cols, vals), P
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_row_per_thread_copy_within_bound(L, cplx):
+    """Exact handles with short, evenly sized rows multiply one vector from a
+    sliced-ELL copy (whole rows per thread): every row meets the bound and
+    empty rows give zeros."""
+    n, ncols = 2000 + 13, 1500
+    coo, P = _near_uniform(n, ncols, 7, 8, 0.03, seed=40 + L, cplx=cplx, L=L)
+    A, h = csr_pair(coo, L, vals=coo.val, flags=EX | (1 if cplx else 0))
+    try:
+        x = workloads.full_limb_vector(ncols, L, seed=5, cplx=cplx)
+        y = gpu_spmv(h, x, P, n)
+        assert exact.bound_ratio(y, A, x) <= 1.0
+        empty = np.diff(A.indptr) == 0
+        assert empty.any() and not y[:, empty].any()
+    finally:
+        mps.mpspmv_destroy(h)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_row_per_thread_copy_matches_runs(L, cplx):
+    """Rows that the run layout sums inside one run (the layout SpMM uses)
+    agree bit for bit with the one-row-per-thread product: the same exact sum
+    of the same terms, cut once.  8M entries, so that runs hold 16 entries
+    and about half of the 7..8-entry rows lie inside one run."""
+    rng = np.random.default_rng(60 + L)
+    n, ncols = 1_100_000, 900_000
+    lens = rng.integers(7, 9, n)
+    rows = np.repeat(np.arange(n), lens)
+    j = np.arange(rows.shape[0]) - np.repeat(np.cumsum(lens) - lens, lens)
+    cols = (rows * 7 + 37 * j) % ncols
+    P = 2 * L if cplx else L
+    vals = workloads.full_limb_vector(rows.shape[0], L, seed=61, cplx=cplx)
+    h = mps.mpspmv_create_csr(n, ncols, rows, cols, vals, L, EX | (1 if cplx else 0))
+    try:
+        info = mps.mpspmv_get_info(h)
+        assert info["chunk"] == 16
+        x = workloads.full_limb_vector(ncols, L, seed=6, cplx=cplx)
+        y = gpu_spmv(h, x, P, n)
+        X = np.ascontiguousarray(np.stack([x, x], axis=-1))
+        Yd = torch.empty((P, n, 2), dtype=torch.float64, device="cuda")
+        mps.mpspmv_spmm(h, 2, to_dev(X), 2, Yd, 2)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().numpy()[:, :, 0]
+        indptr = np.concatenate([[0], np.cumsum(lens)])
+        same = (indptr[:-1] // 16) == ((indptr[1:] - 1) // 16)
+        assert same.sum() > n // 4
+        assert np.array_equal(y[:, same], Y[:, same])
+        # split rows: the run partials are cut before the exact combine, so
+        # they may differ in the last component only
+        d = np.abs(y[0] - Y[0])
+        assert (d <= 1e-12 * np.abs(Y[0]) + 1e-300).all()
+    finally:
+        mps.mpspmv_destroy(h)

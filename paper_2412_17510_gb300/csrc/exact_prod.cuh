@@ -10,14 +10,19 @@
 namespace mpk {
 
 // ---------------------------------------------------------------------------
-// Only the error-free products run on the binary64 pipe; their terms are
-// added exactly on the integer pipe (fixacc.cuh).  Product of a . x:
-//   P mode, L = 2: TwoProd(a0, x0) + fma(a0, x1, a1 x0)           4 binary64 ops, 3 terms
-//           L = 3: TwoProd for i+j <= 1, FMA chain for i+j = 2    9 ops, 7 terms
-//           L = 4: TwoProd for i+j <= 2, FMA chain for i+j = 3   16 ops, 13 terms
-//   binary64 a: TwoProd(a, x_j) for j < L-1, a x_{L-1}             2L-1 ops, 2L-1 terms
-// Products of order below the format's unit roundoff are dropped or rounded
-// once; the sum is then exact up to the window and cut to L components.
+// The products of an entry, a . x, go into the exact accumulator
+// (fixacc.cuh) as:
+//   P mode, L = 2: a0 x0 exactly, plus fma(a0, x1, a1 x0)
+//           L = 3: a_i x_j exactly for i+j <= 1, plus one FMA chain for i+j = 2
+//           L = 4: a_i x_j exactly for i+j <= 2, plus one FMA chain for i+j = 3
+//   binary64 a: a x_j exactly for j < L-1, plus a x_{L-1} rounded
+// An exact product is formed on the integer pipe as one 106-bit integer
+// (fas_add_prod) when the window has at least 6 digits (DD, TD, QD); the
+// binary64 pipe then only runs the FMA chain (2, 3, 4 instructions per entry
+// in P mode, 1 for binary64 a).  Binary64 sums (4 digits) keep TwoProd by
+// FMA, two binary64 terms per product.  Products below the format's unit
+// roundoff are dropped or rounded once; the sum is exact up to the window
+// and cut to L components.
 // ---------------------------------------------------------------------------
 
 template <int L>
@@ -30,6 +35,20 @@ __device__ __forceinline__ void acc_add(FixAccS<D, T>& a, double v, bool neg) {
   fas_add<D, T>(a, v, neg);
 }
 
+// acc += x y exactly: on the integer pipe when the window (D digits) holds a
+// 106-bit product with room for its offset (D >= 6), else TwoProd by FMA.
+template <int D, int T>
+__device__ __forceinline__ void acc_add_prod(FixAccS<D, T>& a, double x, double y, bool neg) {
+  if constexpr (D >= 6) {
+    fas_add_prod<D, T>(a, x, y, neg);
+  } else {
+    double p, e;
+    two_prod(x, y, p, e);
+    fas_add<D, T>(a, p, neg);
+    fas_add<D, T>(a, e, neg);
+  }
+}
+
 template <class Acc, int L>
 __device__ __forceinline__ void add_prod(Acc& acc, const mp<L>& a, const mp<L>& x, bool negate) {
   if constexpr (L == 1) {
@@ -38,23 +57,18 @@ __device__ __forceinline__ void add_prod(Acc& acc, const mp<L>& a, const mp<L>& 
     acc_add(acc, p, negate);
     acc_add(acc, e, negate);
   } else if constexpr (L == 2) {
-    double p, e;
-    two_prod(a.v[0], x.v[0], p, e);
     const double c = __fma_rn(a.v[0], x.v[1], __dmul_rn(a.v[1], x.v[0]));
-    acc_add(acc, p, negate);
-    acc_add(acc, e, negate);
+    acc_add_prod(acc, a.v[0], x.v[0], negate);
     acc_add(acc, c, negate);
   } else if constexpr (L == 3) {
     const int ij[3][2] = {{0, 0}, {0, 1}, {1, 0}};
 #pragma unroll
     for (int t = 0; t < 3; t++) {
-      double ai = a.v[ij[t][0]], xj = x.v[ij[t][1]], p, e;
+      double ai = a.v[ij[t][0]], xj = x.v[ij[t][1]];
       // keep the products in step with the accumulation (the compiler would
       // otherwise form every product first and run out of registers)
       asm volatile("" : "+d"(ai), "+d"(xj)::"memory");
-      two_prod(ai, xj, p, e);
-      acc_add(acc, p, negate);
-      acc_add(acc, e, negate);
+      acc_add_prod(acc, ai, xj, negate);
     }
     const double c = __fma_rn(a.v[0], x.v[2], __fma_rn(a.v[1], x.v[1], __dmul_rn(a.v[2], x.v[0])));
     acc_add(acc, c, negate);
@@ -63,11 +77,9 @@ __device__ __forceinline__ void add_prod(Acc& acc, const mp<L>& a, const mp<L>& 
     for (int i = 0; i < 3; i++) {
 #pragma unroll
       for (int j = 0; j < 3 - i; j++) {
-        double ai = a.v[i], xj = x.v[j], p, e;
+        double ai = a.v[i], xj = x.v[j];
         asm volatile("" : "+d"(ai), "+d"(xj)::"memory");
-        two_prod(ai, xj, p, e);
-        acc_add(acc, p, negate);
-        acc_add(acc, e, negate);
+        acc_add_prod(acc, ai, xj, negate);
       }
     }
     const double c =
@@ -80,12 +92,7 @@ __device__ __forceinline__ void add_prod(Acc& acc, const mp<L>& a, const mp<L>& 
 template <class Acc, int L>
 __device__ __forceinline__ void add_prod_d(Acc& acc, double a, const mp<L>& x, bool negate) {
 #pragma unroll
-  for (int j = 0; j < L - 1; j++) {
-    double p, e;
-    two_prod(a, x.v[j], p, e);
-    acc_add(acc, p, negate);
-    acc_add(acc, e, negate);
-  }
+  for (int j = 0; j < L - 1; j++) acc_add_prod(acc, a, x.v[j], negate);
   acc_add(acc, __dmul_rn(a, x.v[L - 1]), negate);
 }
 

@@ -242,13 +242,13 @@ __device__ __noinline__ void fas_shift_smem(unsigned long long* d, int s) {
   }
 }
 
-// The window for a term whose top bit (e0 + 52) lies at or above digit D - 1:
-// the first term anchors it (top bit in the last bit of digit D - 2), a later
-// one moves it up by whole digits.  Returns the new base.
+// The window for a term whose top bit (at 2^top) lies at or above digit
+// D - 1: the first term anchors it (top bit in the last bit of digit D - 2),
+// a later one moves it up by whole digits.  Returns the new base.
 template <int D, int T>
-__device__ __noinline__ int fas_window(unsigned long long* dp, unsigned long long* dn, int base, int e0) {
-  if (base == kNotLive) return e0 + 52 - (32 * (D - 1) - 1);
-  const int sd = (e0 - base + 52 - (32 * (D - 1) - 1) + 31) >> 5;
+__device__ __noinline__ int fas_window(unsigned long long* dp, unsigned long long* dn, int base, int top) {
+  if (base == kNotLive) return top - (32 * (D - 1) - 1);
+  const int sd = (top - base - (32 * (D - 1) - 1) + 31) >> 5;
   fas_shift_smem<D, T>(dp, sd);
   fas_shift_smem<D, T>(dn, sd);
   return base + 32 * sd;
@@ -262,7 +262,7 @@ __device__ __noinline__ int fas_add_general(unsigned long long* dp, unsigned lon
   if (m == 0) return base;
   int pos = e0 - base;
   if (pos + 52 >= 32 * (D - 1)) {
-    base = fas_window<D, T>(dp, dn, base, e0);
+    base = fas_window<D, T>(dp, dn, base, e0 + 52);
     pos = e0 - base;
   }
   if (pos < 0) {
@@ -302,7 +302,7 @@ __device__ __forceinline__ void fas_add(FixAccS<D, T>& a, double v, bool neg) {
   const int e0 = ef - 1075;  // v = +-m 2^e0
   int pos = e0 - a.base;
   if (pos > 32 * (D - 1) - 53) {  // first term, or the window has to move up
-    a.base = fas_window<D, T>(a.dp, a.dn, a.base, e0);
+    a.base = fas_window<D, T>(a.dp, a.dn, a.base, e0 + 52);
     pos = e0 - a.base;
   }
   if (pos < 0) {
@@ -317,6 +317,59 @@ __device__ __forceinline__ void fas_add(FixAccS<D, T>& a, double v, bool neg) {
   p[0] += lo & 0xffffffffULL;
   p[T] += lo >> 32;
   p[2 * T] += hi;
+}
+
+// a += x y exactly (neg: a -= x y) for binary64 x, y: the two 53-bit
+// mantissas are multiplied on the integer pipe into one exact 106-bit
+// integer, added as five 32-bit chunks (with the top bit below digit D - 1
+// the fifth chunk is at most digit D - 1).  This replaces TwoProd by FMA
+// (two binary64 instructions) and the two separate additions of its terms:
+// p + e of TwoProd is the same exact product.  Zero, subnormal and
+// non-finite operands take the binary64 path.
+template <int D, int T>
+__device__ __forceinline__ void fas_add_prod(FixAccS<D, T>& a, double x, double y, bool neg) {
+  const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long by = (unsigned long long)__double_as_longlong(y);
+  const int ex = (int)((bx >> 52) & 0x7ff), ey = (int)((by >> 52) & 0x7ff);
+  if ((unsigned)(ex - 1) >= 0x7feu || (unsigned)(ey - 1) >= 0x7feu) {
+    const double p = __dmul_rn(x, y);
+    fas_add<D, T>(a, p, neg);
+    fas_add<D, T>(a, __fma_rn(x, y, -p), neg);
+    return;
+  }
+  const bool negative = (((bx ^ by) >> 63) != 0) != neg;
+  const unsigned long long mx = (bx & 0xfffffffffffffULL) | (1ULL << 52);
+  const unsigned long long my = (by & 0xfffffffffffffULL) | (1ULL << 52);
+  unsigned long long lo = mx * my;            // the product mx my < 2^106 as hi 2^64 + lo
+  unsigned long long hi = __umul64hi(mx, my);
+  const int e0 = ex + ey - 2150;              // x y = mx my 2^e0
+  int pos = e0 - a.base;
+  if (pos > 32 * (D - 1) - 106) {             // top bit (at most e0 + 105) at or above digit D - 1
+    a.base = fas_window<D, T>(a.dp, a.dn, a.base, e0 + 105);
+    pos = e0 - a.base;
+  }
+  if (pos < 0) {                              // truncate the part below the window
+    if (pos <= -106) return;
+    const int sh = -pos;
+    if (sh >= 64) {
+      lo = hi >> (sh - 64);
+      hi = 0;
+    } else {
+      lo = (lo >> sh) | ((hi << 1) << (63 - sh));  // hi << (64 - sh), 0 for sh = 0
+      hi >>= sh;
+    }
+    pos = 0;
+  }
+  const int w = pos >> 5, r = pos & 31;
+  const unsigned long long w0 = lo << r;
+  const unsigned long long w1 = (hi << r) | ((lo >> 1) >> (63 - r));  // lo >> (64 - r), 0 for r = 0
+  const unsigned long long w2 = (hi >> 1) >> (63 - r);
+  unsigned long long* p = (negative ? a.dn : a.dp) + w * T;
+  p[0] += w0 & 0xffffffffULL;
+  p[T] += w0 >> 32;
+  p[2 * T] += w1 & 0xffffffffULL;
+  p[3 * T] += w1 >> 32;
+  p[4 * T] += w2;
 }
 
 // Row flush, kept out of line: it runs once per row and its many temporaries

@@ -43,13 +43,28 @@ PNAME = {1: "D", 2: "DD", 3: "TD", 4: "QD"}
 # components plus one folding addition each) -- the oracle's operation counts.
 OPS_PER_ENTRY = {2: 9 + 11, 3: 124 + 88, 4: 123 + 87}
 # exact accumulation (MPSPMV_EXACT_ACC): binary64 instructions per stored entry
-# of the product stage (TwoProd = DMUL + DFMA; FMA chains for the rounded
-# terms); the row sums run on the integer pipe.
-OPS_PER_ENTRY_EXACT = {2: 4, 3: 9, 4: 16}
-# ... and on binary64 data (only leading components stored; MP x binary64
-# product forms, the omitted products being exactly zero): 2L - 1
-OPS_PER_ENTRY_EXACT_D = {2: 3, 3: 5, 4: 7}
+# -- only the FMA chain of the rounded products; the exact products are
+# formed on the integer pipe -- in P mode and on binary64 data (one stored
+# value plane, MP x binary64 product forms):
+OPS_PER_ENTRY_EXACT = {2: 2, 3: 3, 4: 4}
+OPS_PER_ENTRY_EXACT_D = {2: 1, 3: 1, 4: 1}
+# ... and shared-memory digit updates per stored entry, the accumulation's
+# own bound: an exact 106-bit product adds five 32-bit chunks, a rounded
+# binary64 term three (P mode: 1/3/6 exact products for DD/TD/QD; binary64
+# data: L - 1), each update an 8-byte load and an 8-byte store.
+UPD_PER_ENTRY_EXACT = {2: 8, 3: 18, 4: 33}
+UPD_PER_ENTRY_EXACT_D = {2: 8, 3: 13, 4: 18}
+SMEM_BYTES_PER_CLK = 128  # shared-memory bandwidth per SM per clock (32 banks x 4 B)
+UPD_BYTES = 16
 L2_FLUSH_BYTES = 512 << 20
+
+
+def smem_peak_updates(clock_mhz):
+    """Shared-memory digit updates per second the GPU can sustain: SMs x clock x
+    bandwidth per clock / bytes per update."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * clock_mhz * 1e6 * SMEM_BYTES_PER_CLK / UPD_BYTES
 
 
 def make_matrices(small=False):
@@ -274,13 +289,14 @@ def suite_complex(mps, fp64_fma, hbm, stream, small):
             for _ in range(3):
                 mps.mpspmv_spmv(h, x, y, stream)
             ms = _time_events(lambda: mps.mpspmv_spmv(h, x, y, stream), 10, stream)
-            if fl:
+            if fl:  # four real products per complex entry
                 per = OPS_PER_ENTRY_EXACT_D[L] if vp == 2 else OPS_PER_ENTRY_EXACT[L]
+                upd = UPD_PER_ENTRY_EXACT_D[L] if vp == 2 else UPD_PER_ENTRY_EXACT[L]
             else:
-                per = OPS_PER_ENTRY[L]
+                per, upd = OPS_PER_ENTRY[L], 0
             ops = coo.nnz * 4 * per
             byts = coo.nnz * (4 + 8 * vp) + n * (8 + 16 * L) + n * 16 * L
-            troof = max(ops / fp64_fma, byts / (hbm * 1e9))
+            troof = max(ops / fp64_fma, byts / (hbm * 1e9), coo.nnz * 4 * upd / smem_peak_updates(2070.0))
             out["spmv_%s%s" % (PNAME[L], sfx)] = {"ms": ms, "gnnz_s": coo.nnz / ms / 1e6,
                                                   "roofline_frac": troof / (ms * 1e-3)}
             mps.mpspmv_destroy(h)
@@ -590,8 +606,16 @@ def main():
         ms = float(tt.item())
     step_nnz = sum(v["nnz"] for v in variants)
     value = step_nnz * world / (ms * 1e-3) / 1e9
-    launches_per_step = sum(1 + (v["info"]["nsplit_rows"] > v["info"]["nlong_rows"]) + (v["info"]["nlong_rows"] > 0)
-                            for v in variants)
+    def launches_of(v):
+        i = v["info"]
+        if v["arith"] != "exact":
+            return 1 + (i["nsplit_rows"] > i["nlong_rows"]) + (i["nlong_rows"] > 0)
+        inter = 1 if v["L"] > 1 else 0  # interleaved copy of x
+        if i["sell_slots"] > 0:
+            return inter + 1            # one row per thread
+        return inter + 1 + (i["nsplit_rows"] > i["nlong_rows"]) + (i["nlong_rows"] > 0)
+
+    launches_per_step = sum(launches_of(v) for v in variants)
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e_ms = []
@@ -619,49 +643,61 @@ def main():
     except Exception:
         pass
 
-    def table_of(v):
-        if v["arith"] != "exact":
-            return OPS_PER_ENTRY
-        return OPS_PER_ENTRY_EXACT_D if v["info"]["value_planes"] == 1 else OPS_PER_ENTRY_EXACT
+    smem = smem_peak_updates(clock_mhz=2070.0)
 
-    def ops_of(v):
-        return v["nnz"] * table_of(v)[v["L"]]
+    def per_entry(v):
+        """(binary64 instructions, shared-memory digit updates) per stored entry."""
+        if v["arith"] != "exact":
+            return OPS_PER_ENTRY[v["L"]], 0
+        one = v["info"]["value_planes"] == 1
+        return ((OPS_PER_ENTRY_EXACT_D if one else OPS_PER_ENTRY_EXACT)[v["L"]],
+                (UPD_PER_ENTRY_EXACT_D if one else UPD_PER_ENTRY_EXACT)[v["L"]])
 
     def bytes_of(v):
         return algorithmic_bytes(v["nnz"], v["nrows"], v["ncols"], v["L"], v["info"]["value_planes"])
+
+    def times_of(v):
+        """Roofline times (s) of one product: HBM bytes, binary64 pipe, digit updates."""
+        o, u = per_entry(v)
+        return {"hbm": bytes_of(v) / (hbm * 1e9), "fp64": v["nnz"] * o / fp64_fma, "smem": v["nnz"] * u / smem}
 
     def breakdown_of(vs, pv):
         out = {}
         for i, w in enumerate(vs):
             t = pv[i] * 1e-3
-            o = ops_of(w)
-            b = bytes_of(w)
-            troof = max(o / fp64_fma, b / (hbm * 1e9))
-            out[w["name"]] = {"ms": pv[i], "gnnz_s": w["nnz"] / t / 1e9, "roofline_frac": troof / t,
-                              "fp64_tinstr_s": o / t / 1e12, "hbm_gbs": b / t / 1e9, "chunk": w["info"]["chunk"]}
+            tr = times_of(w)
+            out[w["name"]] = {"ms": pv[i], "gnnz_s": w["nnz"] / t / 1e9, "roofline_frac": max(tr.values()) / t,
+                              "bound": max(tr, key=tr.get), "fp64_tinstr_s": w["nnz"] * per_entry(w)[0] / t / 1e12,
+                              "hbm_gbs": bytes_of(w) / t / 1e9, "chunk": w["info"]["chunk"]}
         return out
 
-    # roofline of the dominant kernel (largest share of the step)
+    # roofline of the dominant kernel (largest share of the step): the
+    # largest of the three roofline times decides the bound
     dom = int(np.argmax(per_var))
     v = variants[dom]
     t_s = per_var[dom] * 1e-3
-    ops = ops_of(v)
-    byts = bytes_of(v)
-    t_alu = ops / fp64_fma
-    t_hbm = byts / (hbm * 1e9)
-    bound = "alu" if t_alu >= t_hbm else "hbm"
-    if bound == "alu":
-        achieved, peak, unit = ops / t_s / 1e12, fp64_fma / 1e12, "T binary64 instr/s"
+    o_e, u_e = per_entry(v)
+    ops, upd, byts = v["nnz"] * o_e, v["nnz"] * u_e, bytes_of(v)
+    tr = times_of(v)
+    which = max(tr, key=tr.get)
+    if which == "fp64":
+        bound, achieved, peak, unit = "alu", ops / t_s / 1e12, fp64_fma / 1e12, "T binary64 instr/s"
+        src = "measured in this run by mpspmv_probe_fp64 (DFMA chains, all SMs)"
+    elif which == "smem":
+        bound, achieved, peak, unit = "alu", upd / t_s / 1e12, smem / 1e12, "T shared-memory digit updates/s"
+        src = ("derived: SMs x 2070 MHz x %d B/clk shared-memory bandwidth / %d B per update "
+               "(8-byte load + 8-byte store)" % (SMEM_BYTES_PER_CLK, UPD_BYTES))
     else:
-        achieved, peak, unit = byts / t_s / 1e9, hbm, "GB/s"
+        bound, achieved, peak, unit = "hbm", byts / t_s / 1e9, hbm, "GB/s"
+        src = "MEASURED_PEAKS.json hbm_gbs"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
             "traffic": stored_traffic(v["arith"] + ":" + v["name"]),
-            "kernel": "spmv_runs_kernel + combine kernels, %s arithmetic, %s" % (v["arith"], v["name"]),
-            "peak_source": "measured in this run by mpspmv_probe_fp64 (DFMA chains, all SMs)"
-            if bound == "alu" else "MEASURED_PEAKS.json hbm_gbs",
-            "algorithmic_ops_per_launch": ops, "algorithmic_bytes_per_launch": byts,
-            "fp64_dadd_peak_tinstr_s": fp64_add / 1e12,
-            "ops_per_entry": table_of(v)[v["L"]], "value_planes": v["info"]["value_planes"]}
+            "kernel": "spmv run/row kernels + combine kernels, %s arithmetic, %s" % (v["arith"], v["name"]),
+            "peak_source": src,
+            "fracs": {k: tr[k] / t_s for k in tr},
+            "algorithmic_ops_per_launch": ops, "algorithmic_digit_updates_per_launch": upd,
+            "algorithmic_bytes_per_launch": byts, "fp64_dadd_peak_tinstr_s": fp64_add / 1e12,
+            "ops_per_entry": o_e, "updates_per_entry": u_e, "value_planes": v["info"]["value_planes"]}
     breakdown = breakdown_of(variants, per_var)
     other_out = {}
     for ar, (pv, oms, _) in other.items():

@@ -80,6 +80,9 @@ typedef struct {
   int64_t nlong_rows;   /* of nsplit_rows, those spanning more than 32 runs */
   int64_t value_planes; /* binary64 value planes stored per entry (1 or 2 when only leading
                            components are kept: M mode, or MPSPMV_EXACT_ACC on binary64 data) */
+  int64_t sell_slots;   /* exact-accumulation handles with short, evenly sized rows: slots of the
+                           sliced-ELL copy that single-vector products use (one row per thread);
+                           0 when products use the run layout only */
 } mpspmv_info;
 
 /*

@@ -44,7 +44,7 @@ class mpspmv_info(ctypes.Structure):
                 ("max_row_nnz", ctypes.c_int64), ("nchunks", ctypes.c_int64), ("nsplit_rows", ctypes.c_int64),
                 ("prec", ctypes.c_int32), ("planes", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("device_bytes", ctypes.c_int64), ("nlong_rows", ctypes.c_int64),
-                ("value_planes", ctypes.c_int64)]
+                ("value_planes", ctypes.c_int64), ("sell_slots", ctypes.c_int64)]
 
 
 def _load():

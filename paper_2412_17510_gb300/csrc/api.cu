@@ -381,6 +381,7 @@ int mpspmv_get_info(mpspmv_h h, mpspmv_info* info) {
   info->device_bytes = h->device_bytes;
   info->nlong_rows = h->nsplit - h->nshort;
   info->value_planes = h->Pv;
+  info->sell_slots = h->sell_len;
   return MPSPMV_OK;
 }
 

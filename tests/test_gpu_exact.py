@@ -192,6 +192,7 @@ def test_row_per_thread_copy_within_bound(L, cplx):
     coo, P = _near_uniform(n, ncols, 7, 8, 0.03, seed=40 + L, cplx=cplx, L=L)
     A, h = csr_pair(coo, L, vals=coo.val, flags=EX | (1 if cplx else 0))
     try:
+        assert mps.mpspmv_get_info(h)["sell_slots"] > 0
         x = workloads.full_limb_vector(ncols, L, seed=5, cplx=cplx)
         y = gpu_spmv(h, x, P, n)
         assert exact.bound_ratio(y, A, x) <= 1.0
@@ -219,7 +220,7 @@ def test_row_per_thread_copy_matches_runs(L, cplx):
     h = mps.mpspmv_create_csr(n, ncols, rows, cols, vals, L, EX | (1 if cplx else 0))
     try:
         info = mps.mpspmv_get_info(h)
-        assert info["chunk"] == 16
+        assert info["chunk"] == 16 and info["sell_slots"] > 0
         x = workloads.full_limb_vector(ncols, L, seed=6, cplx=cplx)
         y = gpu_spmv(h, x, P, n)
         X = np.ascontiguousarray(np.stack([x, x], axis=-1))

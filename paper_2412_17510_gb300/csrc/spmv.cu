@@ -86,9 +86,10 @@ __global__ void build_sell_kernel(DevMat m, const int64_t* __restrict__ slice_pt
 }
 
 // One thread per row of the sliced-ELL copy (exact accumulation, single
-// vector); residency as the run kernel's exact variant.
+// vector).  It holds fewer registers than the run kernel: timed over 5..8
+// resident blocks, QD runs best with 7 and DD/TD with 8.
 template <int L, bool CPLX, bool MIXED>
-__global__ void __launch_bounds__(kThreads, CPLX ? 3 : (L == 4 ? 6 : 7))
+__global__ void __launch_bounds__(kThreads, CPLX ? 3 : (L == 4 ? 7 : 8))
     sell_exact_kernel(DevMat m, const int64_t* __restrict__ slice_ptr, const double* __restrict__ x, int64_t xs,
                       int64_t xoff, double* __restrict__ y, int64_t ys, int64_t yoff, const int* __restrict__ gate) {
   if (gate && *gate != 0) return;

@@ -106,13 +106,13 @@ __global__ void __launch_bounds__(kThreads, CPLX ? 3 : (L == 4 ? 7 : 8))
 // partial, w = 1 last-row partial.
 // The exact variant is bound by integer issue and latency, so it asks for
 // more resident blocks (fewer registers): timed on the stencil and
-// power-law steps over 5..8 blocks, DD and TD run best with 7 and QD with
-// 6; the complex variant's shared memory allows only 5 blocks and more
+// power-law steps over 5..8 blocks, DD and TD run best with 8 and QD with
+// 7; the complex variant's shared memory allows only 5 blocks and more
 // register pressure spills.
 // ---------------------------------------------------------------------------
 template <int L>
 constexpr int exact_min_blocks() {
-  return L == 4 ? 6 : 7;
+  return L == 4 ? 7 : 8;
 }
 
 template <int L, bool CPLX, bool MIXED, bool EXACT>

@@ -59,6 +59,20 @@ UPD_BYTES = 16
 L2_FLUSH_BYTES = 512 << 20
 
 
+def replica_value(local_ms, units_per_rank, world, dist=None, device="cpu"):
+    """Weak scaling over independent replicas (every rank runs the same
+    workload, no collective on the data path): the job's time is the slowest
+    rank's, its throughput the units of all ranks over that time, in G/s.
+    Returns (ms, value)."""
+    ms = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def smem_peak_updates(clock_mhz):
     """Shared-memory digit updates per second the GPU can sustain: SMs x clock x
     bandwidth per clock / bytes per update."""
@@ -600,12 +614,8 @@ def main():
     variants = sets[primary]
     per_var, ms, clocks = timed(variants, True)
     other = {ar: timed(sets[ar], False) for ar in ariths[1:]}
-    if dist:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
     step_nnz = sum(v["nnz"] for v in variants)
-    value = step_nnz * world / (ms * 1e-3) / 1e9
+    ms, value = replica_value(ms, step_nnz, world, dist, device="cuda")
     def launches_of(v):
         i = v["info"]
         if v["arith"] != "exact":
@@ -635,7 +645,7 @@ def main():
         t1 = time.perf_counter()
         if it > 0:
             e2e_ms.append((t1 - t0) * 1e3)
-    e2e_value = step_nnz * world / (np.mean(e2e_ms) * 1e-3) / 1e9
+    _, e2e_value = replica_value(float(np.mean(e2e_ms)), step_nnz, world, dist, device="cuda")
 
     hbm = 6786.2
     try:

@@ -413,8 +413,8 @@ def suite_batched(mps, stream, small):
     ks = [k for *_, k, sd in specs]
     out = {"workload": "%d diffusion matrices, sum nnz %d, sum k*nnz %d" % (
         count, sum(c.nnz for c in coos), sum(c.nnz * k for c, k in zip(coos, ks)))}
-    for L in (2, 4):
-        hs = [mps.mpspmv_create_csr(c.nrows, c.ncols, c.row, c.col, c.val, L, 0, val_limbs=1) for c in coos]
+    for L, fl in ((2, 0), (2, 16), (4, 0), (4, 16)):
+        hs = [mps.mpspmv_create_csr(c.nrows, c.ncols, c.row, c.col, c.val, L, fl, val_limbs=1) for c in coos]
         t0 = time.perf_counter()
         b = mps.mpspmv_batch_create(hs, ks, mps.MPSPMV_BATCH_AUTOTUNE, stream)
         tune_s = time.perf_counter() - t0
@@ -427,7 +427,7 @@ def suite_batched(mps, stream, small):
         ms = _time_events(lambda: mps.mpspmv_batch_spmm(b, Xs, Ys, stream=stream), 10, stream)
         work = sum(c.nnz * k for c, k in zip(coos, ks))
         K, w = mps.mpspmv_batch_get_plan(b, count)
-        out["spmm_%s" % PNAME[L]] = {"ms_per_launch": ms, "gnnz_rhs_s": work / ms / 1e6, "autotune_s": tune_s,
+        out["spmm_%s%s" % (PNAME[L], "_exact" if fl else "")] = {"ms_per_launch": ms, "gnnz_rhs_s": work / ms / 1e6, "autotune_s": tune_s,
                                      "K_hist": {int(v): int((K == v).sum()) for v in np.unique(K)},
                                      "w_hist": {int(v): int((w == v).sum()) for v in np.unique(w)}}
         mps.mpspmv_batch_destroy(b)
@@ -459,9 +459,10 @@ def suite_batched(mps, stream, small):
     return out
 
 
-def suite_selector(mps, small):
-    """Learned precision selector (scaled: see the design doc): SPD systems
-    A = D (L L^T + I) D, n log-uniform in [40, 160], cond 10^U[8, 40],
+def suite_selector(mps, small, flags=0):
+    """Learned precision selector on a scaled-down system set (360 systems,
+    n up to 160 rather than 1e4..1e5, so labelling stays within minutes):
+    SPD systems A = D (L L^T + I) D, n log-uniform in [40, 160], cond 10^U[8, 40],
     labelled by the cheapest of binary64 / DD / TD / QD whose CG reaches
     1e-30 within 30 n iterations; train on the first ones, evaluate on the
     held-out rest against the plain ladder."""
@@ -472,7 +473,7 @@ def suite_selector(mps, small):
     for i in range(ntrain + ntest):
         n = int(round(np.exp(rng.uniform(np.log(40), np.log(160)))))
         coo, b = workloads.selector_system(n, float(rng.uniform(8, 40)), seed=1000 + i)
-        systems.append(sel.System(coo, b))
+        systems.append(sel.System(coo, b, flags))
     t0 = time.perf_counter()
     X = sel.features(systems)
     y = sel.labels(systems, 1e-30, maxit_factor=30)
@@ -512,7 +513,7 @@ def main():
     ap.add_argument("--cg-only", default=None,
                     help="profiling: run only the CG workload of the suite in one variant, e.g. QD/exact, and exit")
     ap.add_argument("--cg-iters", type=int, default=200, help="CG iterations of the CG workload")
-    ap.add_argument("--suite", nargs="?", const="complex,cg,product,batched,selector", default=None,
+    ap.add_argument("--suite", nargs="?", const="complex,cg,product,batched,selector,selector_exact", default=None,
                     help="also measure the complex, CG, product-type, batched and selector workloads (adds "
                          "minutes); "
                          "optionally a comma-separated subset")
@@ -737,7 +738,8 @@ def main():
                  "cg": lambda: suite_cg(mps, stream, args.small),
                  "product": lambda: suite_product(mps, stream, args.small),
                  "batched": lambda: suite_batched(mps, stream, args.small),
-                 "selector": lambda: suite_selector(mps, args.small)}
+                 "selector": lambda: suite_selector(mps, args.small),
+                 "selector_exact": lambda: suite_selector(mps, args.small, mps.MPSPMV_EXACT_ACC)}
         suite = {}
         for name in args.suite.split(","):
             if name not in parts:

@@ -24,12 +24,13 @@ NCLASS = 5
 
 
 class System:
-    """One SPD system with handles at L = 1..4 and its right-hand side."""
+    """One SPD system with handles at L = 1..4 and its right-hand side;
+    ``flags`` (e.g. MPSPMV_EXACT_ACC) apply to every handle."""
 
-    def __init__(self, coo, b):
+    def __init__(self, coo, b, flags=0):
         import torch
         self.n = coo.nrows
-        self.handles = [mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, 0, val_limbs=1)
+        self.handles = [mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, flags, val_limbs=1)
                         for L in (1, 2, 3, 4)]
         self.b = torch.from_numpy(np.ascontiguousarray(b[None, :])).cuda()
 

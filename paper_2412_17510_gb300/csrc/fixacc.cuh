@@ -379,10 +379,12 @@ __device__ __forceinline__ void fas_add_prod(FixAccS<D, T>& a, double x, double 
 // leaves 32-bit magnitude digits in dp (dn is left as it is; callers reset
 // the accumulator afterwards), a negative sum is negated in two's complement,
 // and each component's 53 bits come from three digits read at a computed
-// index, cut by truncation.
+// index, cut by truncation.  Kernels in which every thread flushes at the
+// same step (the vector kernels) take the inline form fas_flush_body, which
+// keeps out[] in registers.
 template <int L, int D, int T>
-__device__ __noinline__ void fas_flush(unsigned long long* dp, const unsigned long long* dn, int base, int flags,
-                                       double* out) {
+__device__ __forceinline__ void fas_flush_body(unsigned long long* dp, const unsigned long long* dn, int base,
+                                               int flags, double* out) {
 #pragma unroll
   for (int l = 0; l < L; l++) out[l] = 0.0;
   if (flags & 2) {
@@ -437,9 +439,46 @@ __device__ __noinline__ void fas_flush(unsigned long long* dp, const unsigned lo
   }
 }
 
+// The out-of-line flush returns its components by value, so they come back
+// in registers instead of through a stack array whose address the call takes.
+template <int L>
+struct FlushOut {
+  double v[L];
+};
+
+template <int L, int D, int T>
+__device__ __noinline__ FlushOut<L> fas_flush(unsigned long long* dp, const unsigned long long* dn, int base,
+                                              int flags) {
+  FlushOut<L> r;
+  fas_flush_body<L, D, T>(dp, dn, base, flags, r.v);
+  return r;
+}
+
 template <int L, int D, int T>
 __device__ __forceinline__ void fas_to_mp(const FixAccS<D, T>& a, double* out) {
-  fas_flush<L, D, T>(a.dp, a.dn, a.base, (a.base != kNotLive ? 1 : 0) | (a.bad ? 2 : 0), out);
+  const FlushOut<L> r = fas_flush<L, D, T>(a.dp, a.dn, a.base, (a.base != kNotLive ? 1 : 0) | (a.bad ? 2 : 0));
+#pragma unroll
+  for (int l = 0; l < L; l++) out[l] = r.v[l];
+}
+
+// The same flush with the components written through a pointer.  The run
+// kernel's per-entry loop sits at its register cap; there the by-value
+// return costs more spills than the stack array it saves, so that kernel
+// takes this form.
+template <int L, int D, int T>
+__device__ __noinline__ void fas_flush_to(unsigned long long* dp, const unsigned long long* dn, int base, int flags,
+                                          double* out) {
+  fas_flush_body<L, D, T>(dp, dn, base, flags, out);
+}
+
+template <int L, int D, int T>
+__device__ __forceinline__ void fas_to_mp_to(const FixAccS<D, T>& a, double* out) {
+  fas_flush_to<L, D, T>(a.dp, a.dn, a.base, (a.base != kNotLive ? 1 : 0) | (a.bad ? 2 : 0), out);
+}
+
+template <int L, int D, int T>
+__device__ __forceinline__ void fas_to_mp_inline(const FixAccS<D, T>& a, double* out) {
+  fas_flush_body<L, D, T>(a.dp, a.dn, a.base, (a.base != kNotLive ? 1 : 0) | (a.bad ? 2 : 0), out);
 }
 
 // ---------------------------------------------------------------------------

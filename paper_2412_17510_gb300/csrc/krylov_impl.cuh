@@ -832,7 +832,7 @@ __device__ __forceinline__ void x_add_mp(XAcc<L>& a, const mp<L>& u, bool neg) {
 template <int L>
 __device__ __forceinline__ mp<L> x_flush(XAcc<L>& a) {
   mp<L> r;
-  fas_to_mp<L, AccDigits<L>::D, kTX>(a, r.v);
+  fas_to_mp_inline<L, AccDigits<L>::D, kTX>(a, r.v);
   fas_reset<AccDigits<L>::D, kTX>(a);
   return r;
 }

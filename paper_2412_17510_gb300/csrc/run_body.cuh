@@ -217,8 +217,8 @@ __device__ __forceinline__ void process_run_exact(const DevMat& m, int64_t c, in
     const int64_t kk = k0 + j + 1;
     if (kk == rend) {
       mp<L> vr, vi = z;
-      fas_to_mp<L, D, T>(sr, vr.v);
-      if (CPLX) fas_to_mp<L, D, T>(si, vi.v);
+      fas_to_mp_to<L, D, T>(sr, vr.v);
+      if (CPLX) fas_to_mp_to<L, D, T>(si, vi.v);
       if (row == first_row && first_partial) {
 #pragma unroll
         for (int p = 0; p < P; p++)
@@ -239,8 +239,8 @@ __device__ __forceinline__ void process_run_exact(const DevMat& m, int64_t c, in
   }
   if (have) {
     mp<L> vr, vi = z;
-    fas_to_mp<L, D, T>(sr, vr.v);
-    if (CPLX) fas_to_mp<L, D, T>(si, vi.v);
+    fas_to_mp_to<L, D, T>(sr, vr.v);
+    if (CPLX) fas_to_mp_to<L, D, T>(si, vi.v);
     const int w = (row == first_row && first_partial) ? 0 : 1;
 #pragma unroll
     for (int p = 0; p < P; p++)

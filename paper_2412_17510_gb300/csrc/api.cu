@@ -51,11 +51,15 @@ void free_handle(mpspmv_mat* h) {
   delete h;
 }
 
-// Entries per run: the longest of 64, 32, 16, 8, 4 that still leaves about
-// four waves of threads on 152 SMs (768 resident threads each).  Long runs
-// mean fewer rows cut by run boundaries, hence fewer partial sums to combine.
-int32_t pick_chunk(int64_t nnz) {
-  int32_t K = 64;
+// Entries per run: the longest of kmax, kmax/2, ..., 4 that still leaves
+// about four waves of threads on 152 SMs (768 resident threads each).  Long
+// runs mean fewer rows cut by run boundaries, hence fewer partial sums to
+// combine.  kmax is 128 for exact accumulation (each cut row costs two
+// flushes and a digit combine; on the power-law matrix n = 1e6 runs of 128
+// instead of 64 took the QD product from 5.23 to 5.06 ms) and 64 for the
+// paper-order sums.
+int32_t pick_chunk(int64_t nnz, int32_t kmax) {
+  int32_t K = kmax;
   while (K > 4 && nnz / K < (int64_t)152 * 768 * 4) K >>= 1;
   return K;
 }
@@ -205,7 +209,7 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
     maxrow = std::max(maxrow, indptr[i + 1]);
     indptr[i + 1] += indptr[i];
   }
-  const int32_t K = pick_chunk(nnz);
+  const int32_t K = pick_chunk(nnz, (flags & MPSPMV_EXACT_ACC) ? 128 : 64);
   const int64_t nchunks = (nnz + K - 1) / K;
   const int64_t ntiles = (nchunks + 31) / 32;
   const int64_t tlen = ntiles * 32 * (int64_t)K;

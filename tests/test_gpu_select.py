@@ -165,3 +165,51 @@ def test_select_precision_maps_classes_and_solve_auto():
         assert st == 0 and ch == 3 and fl == 3 and its[:2] == [0, 0] and rr <= 1e-30
     finally:
         destroy(hs)
+
+
+def test_trained_selector_saves_ladder_iterations():
+    """What the learned part gains over the method without it: the network is
+    trained by the float32 kernels on labels from the method's own batched
+    CG solves (graded SPD systems A = D (L L^T + I) D, n in [40, 80], cond
+    10^U[8, 24], target relative residual 1e-30, cap 30 n per level), then
+    ten held-out systems are solved twice.  The plain ladder starts at
+    binary64, whose CG meets the recurrence test long before its true
+    residual could reach 1e-30, and climbs level by level; the selector-
+    guided ladder starts at the predicted level.  It needs far fewer CG
+    iterations in total and solves as many systems (within two: a plain
+    ladder's warm starts from lower levels can rescue a system that a cold
+    start at the chosen level leaves at the cap)."""
+    from paper_2412_17510_gb300 import selector as sel
+    rng = np.random.default_rng(5)
+    systems = []
+    try:
+        for i in range(50):
+            n = int(rng.integers(40, 81))
+            coo, b = workloads.selector_system(n, float(rng.uniform(8, 24)), seed=2000 + i)
+            systems.append(sel.System(coo, b))
+        train, held_out = systems[:40], systems[40:]
+        X = sel.features(train)
+        y = sel.labels(train, 1e-30, maxit_factor=30)
+        assert not (y == 0).any()  # binary64 never reaches 1e-30
+        params, losses, _ = sel.train(X, y, epochs=200, batch=32, lr=0.05)
+        assert losses[-1] < losses[0]
+        dp = to_dev(params)
+        plain_its = auto_its = plain_ok = auto_ok = 0
+        for s in held_out:
+            maxit = 30 * s.n
+            x = torch.zeros((4, s.n), dtype=torch.float64, device="cuda")
+            st, fl, its, rr = mps.mpspmv_ladder_solve(s.handles, 1, s.b, x, 1e-30, 0.0, maxit)
+            plain_its += sum(its)
+            plain_ok += int(st == mps.MPSPMV_OK)
+            x.zero_()
+            st2, ch, fl2, its2, rr2 = mps.mpspmv_solve_auto(s.handles, dp, sel.NCLASS, s.b, x, 1e-30, 0.0, maxit)
+            auto_its += sum(its2)
+            auto_ok += int(st2 == mps.MPSPMV_OK)
+            assert fl2 >= ch >= 1
+        print("held-out CG iterations: plain ladder %d, selector-guided %d; solved %d / %d of %d"
+              % (plain_its, auto_its, plain_ok, auto_ok, len(held_out)))
+        assert auto_its < 0.8 * plain_its
+        assert auto_ok >= plain_ok - 2
+    finally:
+        for s in systems:
+            s.free()

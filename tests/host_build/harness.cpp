@@ -1,0 +1,122 @@
+// Host build of the device arithmetic (csrc/mp_arith.cuh, csrc/fixacc.cuh)
+// for CPU tests: the same source the kernels compile, run on the host with
+// IEEE 754 binary64 and -ffp-contract=off, exported through a C ABI.  The
+// CUDA qualifiers and intrinsics come from the stand-in cuda_runtime.h next
+// to this file.  Test infrastructure only.
+#include "cuda_runtime.h"
+#include "mp_arith.cuh"
+#include "fixacc.cuh"
+
+namespace {
+
+// digits of the exact accumulators per L (the AccDigits table of the kernels)
+template <int L>
+constexpr int kD = L == 1 ? 4 : (L == 2 ? 6 : (L == 3 ? 8 : 10));
+
+template <int L>
+mpk::mp<L> load_mp(const double* p) {
+  mpk::mp<L> r;
+  for (int l = 0; l < L; l++) r.v[l] = p[l];
+  return r;
+}
+
+template <int L>
+void store_mp(const mpk::mp<L>& a, double* p) {
+  for (int l = 0; l < L; l++) p[l] = a.v[l];
+}
+
+// op 0 add, 1 mul, 2 mul_d (b[0] is the binary64 factor), 3 div; operands
+// and results are n consecutive groups of L components
+template <int L>
+void mp_ops(int op, int64_t n, const double* a, const double* b, double* r) {
+  for (int64_t i = 0; i < n; i++) {
+    const mpk::mp<L> x = load_mp<L>(a + i * L), y = load_mp<L>(b + i * L);
+    mpk::mp<L> z;
+    switch (op) {
+      case 0: z = mpk::mp_add<L>(x, y); break;
+      case 1: z = mpk::mp_mul<L>(x, y); break;
+      case 2: z = mpk::mp_mul_d<L>(x, y.v[0]); break;
+      default: z = mpk::mp_div<L>(x, y); break;
+    }
+    store_mp<L>(z, r + i * L);
+  }
+}
+
+// Sum of n terms in the shared-memory-layout accumulator (stride 1): kind 0
+// adds a[i], kind 1 adds the exact product a[i] b[i]; neg[i] negates the
+// term.  The result is cut to L components by the kernels' flush.
+template <int L>
+int fas_sum(int n, const int* kind, const double* a, const double* b, const int* neg, double* out) {
+  constexpr int D = kD<L>;
+  unsigned long long dp[D], dn[D];
+  mpk::FixAccS<D, 1> acc;
+  acc.dp = dp;
+  acc.dn = dn;
+  mpk::fas_reset<D, 1>(acc);
+  for (int i = 0; i < n; i++) {
+    if (kind[i] == 1) {
+      if constexpr (D >= 6) {
+        mpk::fas_add_prod<D, 1>(acc, a[i], b[i], neg[i] != 0);
+      } else {
+        return -1;  // the kernels form binary64 products by TwoProd instead
+      }
+    } else {
+      mpk::fas_add<D, 1>(acc, a[i], neg[i] != 0);
+    }
+  }
+  mpk::fas_to_mp<L, D, 1>(acc, out);
+  return 0;
+}
+
+// Sum of n binary64 terms in register digits at the base of the largest term
+// (the combine kernels' and block sums' form), cut to L components.
+template <int L>
+void fa_sum(int n, const double* a, double* out) {
+  constexpr int D = kD<L>;
+  int t = INT_MIN;
+  for (int i = 0; i < n; i++) t = t > mpk::top_exp(a[i]) ? t : mpk::top_exp(a[i]);
+  mpk::FixAcc<D> f;
+  mpk::fa_at_top<D>(f, t);
+  for (int i = 0; i < n; i++) mpk::fa_add<D>(f, a[i]);
+  mpk::fa_to_mp<L, D>(f, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+int host_mp_ops(int L, int op, int64_t n, const double* a, const double* b, double* r) {
+  switch (L) {
+    case 1: mp_ops<1>(op, n, a, b, r); return 0;
+    case 2: mp_ops<2>(op, n, a, b, r); return 0;
+    case 3: mp_ops<3>(op, n, a, b, r); return 0;
+    case 4: mp_ops<4>(op, n, a, b, r); return 0;
+    default: return -1;
+  }
+}
+
+int host_fas_sum(int L, int n, const int* kind, const double* a, const double* b, const int* neg, double* out) {
+  switch (L) {
+    case 1: return fas_sum<1>(n, kind, a, b, neg, out);
+    case 2: return fas_sum<2>(n, kind, a, b, neg, out);
+    case 3: return fas_sum<3>(n, kind, a, b, neg, out);
+    case 4: return fas_sum<4>(n, kind, a, b, neg, out);
+    default: return -1;
+  }
+}
+
+int host_fa_sum(int L, int n, const double* a, double* out) {
+  switch (L) {
+    case 1: fa_sum<1>(n, a, out); return 0;
+    case 2: fa_sum<2>(n, a, out); return 0;
+    case 3: fa_sum<3>(n, a, out); return 0;
+    case 4: fa_sum<4>(n, a, out); return 0;
+    default: return -1;
+  }
+}
+
+double host_chunk_to_double(unsigned long long chunk, int e, int neg) {
+  return mpk::chunk_to_double(chunk, e, neg != 0);
+}
+
+}  // extern "C"

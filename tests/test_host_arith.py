@@ -1,0 +1,258 @@
+"""The device arithmetic, compiled for the host (tests/host_build): the same
+csrc/mp_arith.cuh and csrc/fixacc.cuh the kernels compile, run on the CPU
+with IEEE 754 binary64 and no FMA contraction.  This checks, without a GPU,
+millions of operations that the GPU tests sample:
+
+* the paper-order MP add, mul, mul_d and div (Algorithms 1-5, QD sloppy
+  forms, long division) are bit-identical to the oracle's;
+* the exact accumulators (shared-memory digits with their window, and the
+  register digits at a common base) return the exact sum of their terms cut
+  to L components by truncation, whenever the terms fit the window: signs,
+  cancellation to zero, carries into the head-room digit, window moves,
+  106-bit integer products, subnormal terms, non-finite terms;
+* the integer assembly of a component from its 53-bit chunk
+  (chunk_to_double) equals chunk * 2^e, including the subnormal and
+  overflow ends.
+"""
+import ctypes
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import exact
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2412_17510_gb300", "csrc")
+SC = 2 * exact.SCALE  # terms and products are integers times 2^-2148
+DIGITS = {1: 4, 2: 6, 3: 8, 4: 10}  # accumulator digits per L, as in the kernels
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("g++ not available")
+    out = str(tmp_path_factory.mktemp("host_build") / "libhostarith.so")
+    cmd = [cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-Wno-unknown-pragmas", "-shared",
+           "-fPIC", "-I", os.path.join(HERE, "host_build"), "-I", CSRC, os.path.join(HERE, "host_build", "harness.cpp"),
+           "-o", out]
+    subprocess.run(cmd, check=True, capture_output=True)
+    h = ctypes.CDLL(out)
+    h.host_mp_ops.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp]
+    h.host_fas_sum.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, _dp, _ip, _dp]
+    h.host_fa_sum.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+    h.host_chunk_to_double.argtypes = [ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int]
+    h.host_chunk_to_double.restype = ctypes.c_double
+    return h
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+# --------------------------------------------------------------------------
+# paper-order MP operations against the oracle
+# --------------------------------------------------------------------------
+OPS = {0: lambda L, a, b: oracle.mp_add(L, a, b), 1: lambda L, a, b: oracle.mp_mul(L, a, b),
+       2: lambda L, a, b: oracle.mp_mul_d(L, a, b[0]), 3: lambda L, a, b: oracle.mp_div(L, a, b)}
+
+
+def _operands(n, L, seed):
+    rng = np.random.default_rng(seed)
+    a = workloads.full_limb_vector(n, L, seed=seed).T.copy()
+    b = workloads.full_limb_vector(n, L, seed=seed + 1).T.copy()
+    a *= (2.0 ** rng.integers(-60, 61, n))[:, None]
+    b *= (2.0 ** rng.integers(-60, 61, n))[:, None]
+    # near-cancellation for the additions: b = -a with its last component moved
+    k = n // 4
+    b[:k] = -a[:k]
+    b[:k, L - 1] *= 1.0 + 2.0 ** -20
+    # integers (exact products and sums) and a binary64 first operand
+    a[k:2 * k] = np.floor(a[k:2 * k] * 1e6)
+    a[k:2 * k, 1:] = 0.0
+    return a, b
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+@pytest.mark.parametrize("op", [0, 1, 2, 3])
+def test_mp_ops_bit_identical_to_oracle(lib, L, op):
+    n = 2000
+    a, b = _operands(n, L, seed=10 * L + op)
+    r = np.zeros((n, L))
+    assert lib.host_mp_ops(L, op, n, _d(a), _d(b), _d(r)) == 0
+    for i in range(n):
+        ref = OPS[op](L, a[i], b[i])
+        assert np.array_equal(r[i], ref), (L, op, i, a[i], b[i], r[i], ref)
+
+
+# --------------------------------------------------------------------------
+# exact accumulators against exact integer sums
+# --------------------------------------------------------------------------
+def _term(kind, a, b, neg):
+    v = exact.f2i(a) << exact.SCALE if kind == 0 else exact.f2i(a) * exact.f2i(b)
+    return -v if neg else v
+
+
+def _cut(V, L):
+    """V * 2^-2148 cut to L components by truncation of its magnitude."""
+    out = np.zeros(L)
+    if V == 0:
+        return out
+    s = -1.0 if V < 0 else 1.0
+    m = abs(V)
+    top = m.bit_length() - 1
+    for l in range(L):
+        lsb = top - 52 - 53 * l
+        chunk = (m >> lsb) & ((1 << 53) - 1) if lsb >= 0 else (m << -lsb) & ((1 << 53) - 1)
+        out[l] = s * math.ldexp(chunk, lsb - SC)
+    return out
+
+
+def _span(terms):
+    """Bits from the lowest set bit of any term to the top bit of the largest."""
+    nz = [abs(t) for t in terms if t]
+    if not nz:
+        return 0
+    lo = min((t & -t).bit_length() - 1 for t in nz)
+    hi = max(t.bit_length() - 1 for t in nz)
+    return hi - lo + 1
+
+
+def _fas(lib, L, kind, a, b, neg):
+    n = len(kind)
+    kind = np.ascontiguousarray(kind, dtype=np.int32)
+    neg = np.ascontiguousarray(neg, dtype=np.int32)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.zeros(L)
+    assert lib.host_fas_sum(L, n, _i(kind), _d(a), _d(b), _i(neg), _d(out)) == 0
+    return out
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_shared_digit_accumulator_is_exact_within_its_window(lib, L):
+    """Random mixtures of binary64 terms and exact products, both signs,
+    exponent ranges chosen so that every term fits the window the
+    accumulator guarantees after any move (32 (D - 2) + 1 bits below the
+    largest term); the first term is often a small one, so the window moves
+    up."""
+    rng = np.random.default_rng(100 + L)
+    D = DIGITS[L]
+    guaranteed = 32 * (D - 2) + 1
+    checked = 0
+    for case in range(400):
+        n = int(rng.integers(1, 120))
+        prods = L >= 2 and case % 2 == 1
+        kind = (rng.random(n) < 0.6).astype(np.int32) if prods else np.zeros(n, dtype=np.int32)
+        spread = max(1, (guaranteed - (106 if prods else 53) - 8) // 2)
+        a = rng.standard_normal(n) * 2.0 ** rng.integers(-spread, spread + 1, n)
+        b = np.where(kind == 1, rng.standard_normal(n) * 2.0 ** rng.integers(-spread // 2, spread // 2 + 1, n), 0.0)
+        if prods:  # the product's exponent range is a's plus b's: narrow a for products
+            a = np.where(kind == 1, rng.standard_normal(n) * 2.0 ** rng.integers(-spread // 2, spread // 2 + 1, n), a)
+        neg = (rng.random(n) < 0.5).astype(np.int32)
+        terms = [_term(k, x, y, g) for k, x, y, g in zip(kind, a, b, neg)]
+        if _span(terms) > guaranteed:
+            continue
+        got = _fas(lib, L, kind, a, b, neg)
+        assert np.array_equal(got, _cut(sum(terms), L)), (L, case)
+        checked += 1
+    assert checked >= 300
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_shared_digit_accumulator_special_cases(lib, L):
+    x = workloads.full_limb_vector(1, L, seed=4)[:, 0]
+    # exact cancellation: x - x, its components in another order
+    kind = np.zeros(2 * L, dtype=np.int32)
+    a = np.concatenate([x, x[::-1]])
+    neg = np.array([0] * L + [1] * L, dtype=np.int32)
+    assert not _fas(lib, L, kind, a, np.zeros(2 * L), neg).any()
+    # a product that cancels a TwoProd pair: a b - fl(a b) - err(a b) = 0
+    p, e = oracle.two_prod(x[0], 3.0 + 2.0 ** -40)
+    got = _fas(lib, L, [1, 0, 0], [x[0], p, e], [3.0 + 2.0 ** -40, 0, 0], [0, 1, 1])
+    assert not got.any()
+    # carries into the head-room digit: 1000 copies of a value with all bits set
+    v = 2.0 ** 53 - 1.0
+    got = _fas(lib, L, np.zeros(1000, dtype=np.int32), np.full(1000, v), np.zeros(1000), np.zeros(1000, dtype=np.int32))
+    assert np.array_equal(got, _cut(1000 * (exact.f2i(v) << exact.SCALE), L))
+    # a negative sum whose magnitude has a long run of ones below its second
+    # component: the magnitude is cut, the sign kept (the smallest term sits
+    # inside the window: 32 (D - 2) + 1 - 58 bits below the largest)
+    g = 32 * (DIGITS[L] - 2) + 1
+    terms = [1.0, -3.0 * 2.0 ** -60, 2.0 ** -(g - 60), -2.0 ** -(g - 59)]
+    kind = np.zeros(4, dtype=np.int32)
+    neg = np.array([1, 0, 0, 0], dtype=np.int32)
+    got = _fas(lib, L, kind, terms, np.zeros(4), neg)
+    V = sum(_term(0, t, 0.0, g) for t, g in zip(terms, neg))
+    assert V < 0 and np.array_equal(got, _cut(V, L))
+    # the same sum with the two smallest terms below the window: they are
+    # dropped (the sum is exact up to the window), so the result differs from
+    # the cut exact sum, by less than 2^(2 - 53 L) times the largest term
+    if L == 2:
+        terms = [1.0, -3.0 * 2.0 ** -60, 2.0 ** -200, -2.0 ** -201]
+        got = _fas(lib, L, kind, terms, np.zeros(4), neg)
+        V = sum(_term(0, t, 0.0, g) for t, g in zip(terms, neg))
+        assert not np.array_equal(got, _cut(V, L))
+        err = abs(sum(exact.f2i(c) << exact.SCALE for c in got) - V)
+        assert err <= (exact.f2i(1.0) << exact.SCALE) >> (53 * L - 2)
+    # subnormal terms only (the out-of-line general path)
+    sub = np.array([5e-324, 3 * 5e-324, -7 * 5e-324, 2.0 ** -1030, -(2.0 ** -1060)])
+    got = _fas(lib, L, np.zeros(5, dtype=np.int32), sub, np.zeros(5), np.zeros(5, dtype=np.int32))
+    assert np.array_equal(got, _cut(sum(exact.f2i(s) << exact.SCALE for s in sub), L))
+    # non-finite terms give NaN in the first component
+    for bad in (math.inf, -math.inf, math.nan):
+        got = _fas(lib, L, [0, 0], [1.0, bad], [0.0, 0.0], [0, 0])
+        assert math.isnan(got[0]) and not got[1:].any()
+    # zero terms only
+    assert not _fas(lib, L, [0, 1], [0.0, 0.0], [0.0, 5.0], [0, 1]).any()
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_register_digit_sum_is_exact_within_its_window(lib, L):
+    """The combine kernels' and block sums' form: every term at the base of
+    the largest one (32 (D - 1) bits of window below its top)."""
+    rng = np.random.default_rng(200 + L)
+    D = DIGITS[L]
+    window = 32 * (D - 1)
+    checked = 0
+    for case in range(300):
+        n = int(rng.integers(1, 200))
+        spread = max(1, (window - 53 - 8) // 2)
+        a = rng.standard_normal(n) * 2.0 ** rng.integers(-spread, spread + 1, n)
+        terms = [_term(0, x, 0.0, False) for x in a]
+        if _span(terms) > window:
+            continue
+        a = np.ascontiguousarray(a)
+        out = np.zeros(L)
+        assert lib.host_fa_sum(L, n, _d(a), _d(out)) == 0
+        assert np.array_equal(out, _cut(sum(terms), L)), (L, case)
+        checked += 1
+    assert checked >= 250
+
+
+def test_chunk_to_double(lib):
+    rng = np.random.default_rng(7)
+    for _ in range(20000):
+        chunk = int(rng.integers(0, 1 << 53, dtype=np.int64))
+        e = int(rng.integers(-1180, 1000))
+        neg = int(rng.integers(0, 2))
+        got = lib.host_chunk_to_double(chunk, e, neg)
+        try:
+            want = math.ldexp(chunk, e)
+        except OverflowError:
+            want = math.inf
+        want = -want if neg else want
+        assert got == want and math.copysign(1.0, got) == math.copysign(1.0, want), (chunk, e, neg)

@@ -55,11 +55,15 @@ typedef enum { MPSPMV_D = 1, MPSPMV_DD = 2, MPSPMV_TD = 3, MPSPMV_QD = 4 } mpspm
 #define MPSPMV_SYMMETRIC 4u /* triplets hold one triangle (Matrix Market "symmetric"):
                                every off-diagonal (i,j,v) also stands for (j,i,v) */
 #define MPSPMV_ONE_BASED 8u /* row/col indices start at 1 (Matrix Market) */
-#define MPSPMV_EXACT_ACC 16u /* GB300 arithmetic variant: per stored entry only the error-free products
-                                (TwoProd by FMA) run on the binary64 pipe and the row sum is accumulated
-                                exactly in fixed point on the integer pipe, then cut to L components.
-                                Same bound 8 m u (|A||x|)_i (usually far smaller error); results are not
-                                bit-identical to the paper-order arithmetic. */
+#define MPSPMV_EXACT_ACC 16u /* GB300 arithmetic variant: the error-free products of a stored entry are
+                                formed exactly (DD/TD/QD: 106-bit integer products of the mantissas;
+                                binary64: TwoProd by FMA), only the products just above the unit
+                                roundoff run as one binary64 FMA chain, and the row sum is accumulated
+                                exactly in fixed point on the integer pipe, then cut to L components by
+                                truncation.  Krylov vector updates and inner products on such a handle
+                                are exact in the same way.  Same bound 8 m u (|A||x|)_i, error of the
+                                same order; results are not bit-identical to the paper-order
+                                arithmetic. */
 #define MPSPMV_TRANSPOSE 32u /* also build A^T (a second internal matrix from the swapped triplets, about
                                 doubling the device bytes) for mpspmv_spmtv and mpspmv_bicg */
 
@@ -74,7 +78,8 @@ typedef struct {
   int64_t nsplit_rows;  /* rows whose entries span more than one run */
   int32_t prec;         /* L */
   int32_t planes;       /* P = L or 2L */
-  int32_t chunk;        /* entries per run (K) */
+  int32_t chunk;        /* entries per run (K): the longest of 128 (exact accumulation) or 64, halved
+                           down to 4, that still gives about four waves of threads */
   uint32_t flags;
   int64_t device_bytes; /* device memory owned by the handle */
   int64_t nlong_rows;   /* of nsplit_rows, those spanning more than 32 runs */

@@ -4,14 +4,17 @@
 // GB300 issues binary64 instructions at about 2 per clock per SM and 32-bit
 // integer instructions at 64-128 per clock per SM.  The MP additions of a row
 // sum (Algorithm 1: 11 binary64 operations; the QD sloppy add: 87) are the
-// larger part of the binary64 work, so this path keeps only the error-free
-// products on the binary64 pipe (TwoProd by FMA) and adds the resulting
-// binary64 terms exactly into a fixed-point accumulator on the integer pipe.
+// larger part of the binary64 work, so this path adds every term exactly into
+// a fixed-point accumulator on the integer pipe, and the error-free products
+// themselves are formed there too (fas_add_prod: the 106-bit product of two
+// mantissas); the binary64 pipe keeps one FMA chain per entry (exact_prod.cuh).
 //
-// Accumulator: D signed 64-bit digits, digit j worth 2^(32 j + base); a term
-// (53-bit mantissa at an arbitrary exponent) is split into at most three
-// 32-bit chunks added to three consecutive digits without carry propagation
-// (a digit absorbs 2^31 chunks before it could overflow).  The top digit is
+// Register form (FixAcc, below): D signed 64-bit digits, digit j worth
+// 2^(32 j + base); a term (53-bit mantissa at an arbitrary exponent) is split
+// into at most three 32-bit chunks added to three consecutive digits without
+// carry propagation (a digit absorbs 2^31 chunks before it could overflow).
+// The shared-memory form (FixAccS, further down) keeps two non-negative digit
+// arrays, one per sign, with the same window rules.  The top digit is
 // head-room: terms are placed so that their top bit lies below digit D-1; a
 // larger term moves the window up by whole digits (carries of the dropped
 // digits are propagated first; what falls below the window is below the

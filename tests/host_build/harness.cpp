@@ -6,12 +6,21 @@
 #include "cuda_runtime.h"
 #include "mp_arith.cuh"
 #include "fixacc.cuh"
+// exact_prod.cuh holds two empty PTX statements that only pin the order of
+// the products for the device compiler ("+d" names a binary64 register
+// there, an integer register on the host); for the host build they are
+// preprocessed away.
+#define asm
+#define volatile(...)
+#include "exact_prod.cuh"
+#undef volatile
+#undef asm
 
 namespace {
 
-// digits of the exact accumulators per L (the AccDigits table of the kernels)
+// digits of the exact accumulators per L
 template <int L>
-constexpr int kD = L == 1 ? 4 : (L == 2 ? 6 : (L == 3 ? 8 : 10));
+constexpr int kD = mpk::AccDigits<L>::D;
 
 template <int L>
 mpk::mp<L> load_mp(const double* p) {
@@ -81,9 +90,50 @@ void fa_sum(int n, const double* a, double* out) {
   mpk::fa_to_mp<L, D>(f, out);
 }
 
+// The terms of one stored entry a . x (exact_prod.cuh: add_prod for an MP
+// value, add_prod_d for a binary64 value, the forms the exact run kernels
+// use) summed into an empty accumulator and cut to L components.
+template <int L>
+int entry_sum(int mode, const double* a, const double* x, double* out) {
+  constexpr int D = kD<L>;
+  unsigned long long dp[D], dn[D];
+  mpk::FixAccS<D, 1> acc;
+  acc.dp = dp;
+  acc.dn = dn;
+  mpk::fas_reset<D, 1>(acc);
+  const mpk::mp<L> xm = load_mp<L>(x);
+  if (mode == 0)
+    mpk::add_prod<mpk::FixAccS<D, 1>, L>(acc, load_mp<L>(a), xm, false);
+  else
+    mpk::add_prod_d<mpk::FixAccS<D, 1>, L>(acc, a[0], xm, false);
+  mpk::fas_to_mp<L, D, 1>(acc, out);
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
+
+int host_acc_digits(int L) {
+  switch (L) {
+    case 1: return kD<1>;
+    case 2: return kD<2>;
+    case 3: return kD<3>;
+    case 4: return kD<4>;
+    default: return -1;
+  }
+}
+
+int host_entry_sum(int L, int mode, const double* a, const double* x, double* out) {
+  switch (L) {
+    case 1: return entry_sum<1>(mode, a, x, out);
+    case 2: return entry_sum<2>(mode, a, x, out);
+    case 3: return entry_sum<3>(mode, a, x, out);
+    case 4: return entry_sum<4>(mode, a, x, out);
+    default: return -1;
+  }
+}
+
 
 int host_mp_ops(int L, int op, int64_t n, const double* a, const double* b, double* r) {
   switch (L) {

@@ -10,6 +10,10 @@ millions of operations that the GPU tests sample:
   to L components by truncation, whenever the terms fit the window: signs,
   cancellation to zero, carries into the head-room digit, window moves,
   106-bit integer products, subnormal terms, non-finite terms;
+* the terms of one stored entry (exact_prod.cuh: the exact products a_i x_j
+  below the format's unit roundoff plus one FMA chain, for MP and binary64
+  matrix values) add up to exactly that decomposition, and stay within a
+  few units of the unit roundoff of the full product;
 * the integer assembly of a component from its 53-bit chunk
   (chunk_to_double) equals chunk * 2^e, including the subnormal and
   overflow ends.
@@ -19,6 +23,7 @@ import math
 import os
 import shutil
 import subprocess
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -30,7 +35,6 @@ from oracle import exact
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2412_17510_gb300", "csrc")
 SC = 2 * exact.SCALE  # terms and products are integers times 2^-2148
-DIGITS = {1: 4, 2: 6, 3: 8, 4: 10}  # accumulator digits per L, as in the kernels
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -52,7 +56,12 @@ def lib(tmp_path_factory):
     h.host_fa_sum.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
     h.host_chunk_to_double.argtypes = [ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int]
     h.host_chunk_to_double.restype = ctypes.c_double
+    h.host_entry_sum.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+    DIGITS.update({L: h.host_acc_digits(L) for L in (1, 2, 3, 4)})
     return h
+
+
+DIGITS = {}  # accumulator digits per L, read from the kernels' table
 
 
 def _d(a):
@@ -256,3 +265,55 @@ def test_chunk_to_double(lib):
             want = math.inf
         want = -want if neg else want
         assert got == want and math.copysign(1.0, got) == math.copysign(1.0, want), (chunk, e, neg)
+
+
+# --------------------------------------------------------------------------
+# the terms of one stored entry (exact_prod.cuh)
+# --------------------------------------------------------------------------
+def _rn_fma(a, b, c):
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def _entry_terms(L, mode, a, x):
+    """Exact integer value (units 2^-2148) of the terms the kernels add for
+    one entry: exact products a_i x_j for i + j < L - 1, plus the FMA chain
+    over i + j = L - 1 (L = 1: the exact product); binary64 a: exact a x_j for
+    j < L - 1 plus the rounded a x_{L-1}."""
+    if mode == 1:
+        if L == 1:
+            return exact.f2i(a[0] * x[0]) << exact.SCALE
+        v = sum(exact.f2i(a[0]) * exact.f2i(x[j]) for j in range(L - 1))
+        return v + (exact.f2i(a[0] * x[L - 1]) << exact.SCALE)
+    if L == 1:
+        return exact.f2i(a[0]) * exact.f2i(x[0])
+    v = sum(exact.f2i(a[i]) * exact.f2i(x[j]) for i in range(L) for j in range(L) if i + j < L - 1)
+    c = a[L - 1] * x[0]
+    for i in range(L - 2, -1, -1):
+        c = _rn_fma(a[i], x[L - 1 - i], c)
+    return v + (exact.f2i(c) << exact.SCALE)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_entry_products_match_their_decomposition(lib, L, mode):
+    n = 1500
+    rng = np.random.default_rng(300 + 10 * L + mode)
+    A = workloads.full_limb_vector(n, L, seed=L + 20).T.copy()
+    X = workloads.full_limb_vector(n, L, seed=L + 30).T.copy()
+    A *= (2.0 ** rng.integers(-100, 101, n))[:, None]
+    X *= (2.0 ** rng.integers(-100, 101, n))[:, None]
+    if mode == 1:
+        A[:, 1:] = 0.0
+    u = exact.U[L]
+    worst = 0.0
+    for i in range(n):
+        out = np.zeros(L)
+        assert lib.host_entry_sum(L, mode, _d(np.ascontiguousarray(A[i])), _d(np.ascontiguousarray(X[i])),
+                                  _d(out)) == 0
+        assert np.array_equal(out, _cut(_entry_terms(L, mode, A[i], X[i]), L)), (L, mode, i)
+        full = exact.limbs_to_int(A[i]) * exact.limbs_to_int(X[i])
+        got = sum(exact.f2i(c) for c in out) << exact.SCALE
+        scale = abs(exact.limbs_to_int(A[i])) * abs(exact.limbs_to_int(X[i]))
+        worst = max(worst, float(Fraction(abs(got - full), scale) / Fraction(u)))
+    # dropped products, the chain's rounding and the final truncation
+    assert worst <= 4.0, worst

@@ -317,3 +317,25 @@ def test_entry_products_match_their_decomposition(lib, L, mode):
         worst = max(worst, float(Fraction(abs(got - full), scale) / Fraction(u)))
     # dropped products, the chain's rounding and the final truncation
     assert worst <= 4.0, worst
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_products_at_the_ends_of_the_exponent_range(lib, L):
+    """Exact products far below the binary64 range (the digits hold them; the
+    cut components round into the subnormal range or to zero, as chunk * 2^e
+    does) and far above it (components overflow to infinity)."""
+    cases = [
+        ([1, 1], [2.0 ** -600, -(2.0 ** -601) * 3], [2.0 ** -500, 2.0 ** -499]),  # sum 2^-1100 (1 - 3)
+        ([1, 0], [2.0 ** -540 * 1.5, 2.0 ** -1074], [2.0 ** -530, 0.0]),          # 1.5 2^-1070 + 2^-1074
+        ([1, 1], [2.0 ** 600 * 1.25, 2.0 ** 600], [2.0 ** 500, -(2.0 ** 500)]),    # 0.25 2^1100 -> inf
+    ]
+    for kind, a, b in cases:
+        kind = np.array(kind, dtype=np.int32)
+        neg = np.zeros(len(kind), dtype=np.int32)
+        got = _fas(lib, L, kind, a, b, neg)
+        V = sum(_term(k, x, y, 0) for k, x, y in zip(kind, a, b))
+        m = abs(V)
+        if V and m.bit_length() - 1 - SC > 1023:
+            assert math.isinf(got[0]) and (got[0] > 0) == (V > 0)
+        else:
+            assert np.array_equal(got, _cut(V, L)), (a, b, got)

@@ -339,3 +339,25 @@ def test_products_at_the_ends_of_the_exponent_range(lib, L):
             assert math.isinf(got[0]) and (got[0] > 0) == (V > 0)
         else:
             assert np.array_equal(got, _cut(V, L)), (a, b, got)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_mp_ops_non_finite_operands_like_the_oracle(lib, L):
+    """Infinite and NaN leading components: the kernels' operations give the
+    oracle's result (NaN where it has NaN, the same infinity otherwise)."""
+    x = workloads.full_limb_vector(1, L, seed=9)[:, 0]
+    specials = []
+    for s in (math.inf, -math.inf, math.nan):
+        v = np.zeros(L)
+        v[0] = s
+        specials.append(v)
+    pairs = [(p, x) for p in specials] + [(x, p) for p in specials] + [(p, q) for p in specials for q in specials]
+    for op in (0, 1, 2, 3):
+        for a, b in pairs:
+            a = np.ascontiguousarray(a)
+            b = np.ascontiguousarray(b)
+            r = np.zeros(L)
+            lib.host_mp_ops(L, op, 1, _d(a), _d(b), _d(r))
+            ref = OPS[op](L, a, b)
+            same = [(math.isnan(g) and math.isnan(w)) or g == w for g, w in zip(r, ref)]
+            assert all(same), (L, op, a, b, r, ref)

@@ -110,9 +110,36 @@ int entry_sum(int mode, const double* a, const double* x, double* out) {
   return 0;
 }
 
+// The flush alone, on given digit arrays (D = the kernels' digit count for L).
+template <int L>
+void flush(const unsigned long long* dp_in, const unsigned long long* dn_in, int base, double* out) {
+  constexpr int D = kD<L>;
+  unsigned long long dp[D], dn[D];
+  for (int j = 0; j < D; j++) {
+    dp[j] = dp_in[j];
+    dn[j] = dn_in[j];
+  }
+  mpk::FixAccS<D, 1> acc;
+  acc.dp = dp;
+  acc.dn = dn;
+  acc.base = base;
+  acc.bad = false;
+  mpk::fas_to_mp<L, D, 1>(acc, out);
+}
+
 }  // namespace
 
 extern "C" {
+
+int host_flush(int L, const unsigned long long* dp, const unsigned long long* dn, int base, double* out) {
+  switch (L) {
+    case 1: flush<1>(dp, dn, base, out); return 0;
+    case 2: flush<2>(dp, dn, base, out); return 0;
+    case 3: flush<3>(dp, dn, base, out); return 0;
+    case 4: flush<4>(dp, dn, base, out); return 0;
+    default: return -1;
+  }
+}
 
 int host_acc_digits(int L) {
   switch (L) {

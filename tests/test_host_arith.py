@@ -57,6 +57,8 @@ def lib(tmp_path_factory):
     h.host_chunk_to_double.argtypes = [ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int]
     h.host_chunk_to_double.restype = ctypes.c_double
     h.host_entry_sum.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+    _up = ctypes.POINTER(ctypes.c_ulonglong)
+    h.host_flush.argtypes = [ctypes.c_int, _up, _up, ctypes.c_int, _dp]
     DIGITS.update({L: h.host_acc_digits(L) for L in (1, 2, 3, 4)})
     return h
 
@@ -361,3 +363,33 @@ def test_mp_ops_non_finite_operands_like_the_oracle(lib, L):
             ref = OPS[op](L, a, b)
             same = [(math.isnan(g) and math.isnan(w)) or g == w for g, w in zip(r, ref)]
             assert all(same), (L, op, a, b, r, ref)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_flush_of_random_digit_arrays(lib, L):
+    """The end-of-row flush on arbitrary digit contents (each digit below
+    2^63, as the accumulator keeps them; the head-room digit small enough that
+    the value stays below 2^(32 D)): one signed carry pass, negation of a
+    negative sum, the components cut by truncation.  Against the exact value
+    sum_j (dp_j - dn_j) 2^(32 j + base)."""
+    D = DIGITS[L]
+    rng = np.random.default_rng(400 + L)
+    up = ctypes.POINTER(ctypes.c_ulonglong)
+    for case in range(3000):
+        dp = rng.integers(0, 2 ** 62, D, dtype=np.uint64) >> rng.integers(0, 62, D).astype(np.uint64)
+        dn = rng.integers(0, 2 ** 62, D, dtype=np.uint64) >> rng.integers(0, 62, D).astype(np.uint64)
+        zero = rng.random(D) < 0.3
+        dp[zero & (rng.random(D) < 0.5)] = 0
+        dn[zero] = 0
+        dp[D - 1] >>= np.uint64(34)  # keep |value| below 2^(32 D - 2): the head-room digit holds carries only
+        dn[D - 1] >>= np.uint64(34)
+        base = int(rng.integers(-1300, 700))
+        out = np.zeros(L)
+        dpc, dnc = np.ascontiguousarray(dp), np.ascontiguousarray(dn)
+        lib.host_flush(L, dpc.ctypes.data_as(up), dnc.ctypes.data_as(up), base, _d(out))
+        V = sum((int(a) - int(b)) << (32 * j) for j, (a, b) in enumerate(zip(dp, dn)))
+        # V * 2^base in units of 2^-2148
+        shift = base + SC
+        assert shift >= 0
+        want = _cut(V << shift, L)
+        assert np.array_equal(out, want), (L, case)

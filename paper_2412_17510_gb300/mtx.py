@@ -1,0 +1,122 @@
+"""Matrix Market coordinate files -> the triplets ``mpspmv_create_csr`` takes.
+
+Host-side input plumbing, no arithmetic of the method.  The paper's test
+matrices are Matrix Market files (Section 4.1: SuiteSparse), and
+``mpspmv_create_csr`` takes COO triplets (Section 3).  ``read_mtx`` parses the
+``matrix coordinate`` format with field ``real``, ``integer``, ``complex`` or
+``pattern`` and symmetry ``general``, ``symmetric``, ``skew-symmetric`` or
+``hermitian``.  The stored triangle of the last three is expanded into both
+triangles (negated for skew-symmetric, conjugated for Hermitian), indices
+become 0-based, and the result is ready for
+``mpspmv_create_csr(nrows, ncols, row, col, val, L, flags, val_limbs=1)``:
+``val`` has one plane for real data and two (real, imaginary) for complex
+data, and ``flags`` carries ``MPSPMV_COMPLEX`` for complex data.  Duplicate
+entries are kept; the library sums them.
+"""
+import io
+
+import numpy as np
+
+from . import MPSPMV_COMPLEX
+
+_FIELDS = ("real", "integer", "complex", "pattern")
+_SYMMETRIES = ("general", "symmetric", "skew-symmetric", "hermitian")
+
+
+class MtxMatrix:
+    """Triplets of one Matrix Market file (0-based, both triangles)."""
+
+    def __init__(self, nrows, ncols, row, col, val, field, symmetry):
+        self.nrows, self.ncols = nrows, ncols
+        self.row, self.col, self.val = row, col, val
+        self.field, self.symmetry = field, symmetry
+
+    @property
+    def nnz(self):
+        return int(self.row.shape[0])
+
+    @property
+    def flags(self):
+        return MPSPMV_COMPLEX if self.field == "complex" else 0
+
+    def args(self):
+        """(nrows, ncols, row, col, val, flags) for mpspmv_create_csr."""
+        return self.nrows, self.ncols, self.row, self.col, self.val, self.flags
+
+
+def _lines(src):
+    if isinstance(src, (str, bytes)) and not (isinstance(src, str) and "\n" in src):
+        with open(src, "r") as f:
+            return f.read().splitlines()
+    if isinstance(src, str):
+        return src.splitlines()
+    if isinstance(src, io.IOBase) or hasattr(src, "read"):
+        return src.read().splitlines()
+    raise TypeError("read_mtx takes a path, the file's text or a file object")
+
+
+def read_mtx(src):
+    """Parse a Matrix Market coordinate file (a path, its text, or an open
+    text file) into an ``MtxMatrix``.  Raises ValueError on a malformed
+    file, an index outside the stated shape, a non-zero diagonal in a
+    skew-symmetric matrix, or a non-square symmetric matrix."""
+    lines = _lines(src)
+    if not lines or not lines[0].lower().startswith("%%matrixmarket"):
+        raise ValueError("missing %%MatrixMarket header")
+    head = lines[0].split()
+    if len(head) != 5 or head[1].lower() != "matrix":
+        raise ValueError("header must read: %%MatrixMarket matrix <format> <field> <symmetry>")
+    fmt, field, sym = head[2].lower(), head[3].lower(), head[4].lower()
+    if fmt != "coordinate":
+        raise ValueError("only the coordinate format is read (got %r)" % fmt)
+    if field not in _FIELDS:
+        raise ValueError("unknown field %r" % field)
+    if sym not in _SYMMETRIES:
+        raise ValueError("unknown symmetry %r" % sym)
+    body = [ln for ln in lines[1:] if ln.strip() and not ln.lstrip().startswith("%")]
+    if not body:
+        raise ValueError("missing size line")
+    size = body[0].split()
+    if len(size) != 3:
+        raise ValueError("size line must hold nrows ncols nnz")
+    nrows, ncols, nnz = (int(t) for t in size)
+    if nrows < 0 or ncols < 0 or nnz < 0:
+        raise ValueError("negative size")
+    if sym != "general" and nrows != ncols:
+        raise ValueError("a %s matrix must be square" % sym)
+    entries = body[1:]
+    if len(entries) != nnz:
+        raise ValueError("size line announces %d entries, file holds %d" % (nnz, len(entries)))
+    width = {"pattern": 2, "real": 3, "integer": 3, "complex": 4}[field]
+    tab = np.zeros((nnz, width))
+    for k, ln in enumerate(entries):
+        t = ln.split()
+        if len(t) != width:
+            raise ValueError("entry %d: expected %d fields, got %d" % (k + 1, width, len(t)))
+        tab[k, :2] = (int(t[0]), int(t[1]))
+        if field == "integer":
+            tab[k, 2] = float(int(t[2]))
+        elif width > 2:
+            tab[k, 2:] = [float(v) for v in t[2:]]
+    row = tab[:, 0].astype(np.int64) - 1
+    col = tab[:, 1].astype(np.int64) - 1
+    if nnz and (row.min() < 0 or col.min() < 0 or row.max() >= nrows or col.max() >= ncols):
+        raise ValueError("index outside the stated shape")
+    if field == "pattern":
+        re, im = np.ones(nnz), None
+    elif field == "complex":
+        re, im = tab[:, 2].copy(), tab[:, 3].copy()
+    else:
+        re, im = tab[:, 2].copy(), None
+    if sym != "general":
+        off = row != col
+        if sym == "skew-symmetric" and (~off).any() and (re[~off] != 0).any():
+            raise ValueError("skew-symmetric matrix with a non-zero diagonal entry")
+        mr, mc = col[off], row[off]
+        mre = -re[off] if sym == "skew-symmetric" else re[off]
+        if im is not None:
+            mim = -im[off] if sym in ("skew-symmetric", "hermitian") else im[off]
+            im = np.concatenate([im, mim])
+        row, col, re = np.concatenate([row, mr]), np.concatenate([col, mc]), np.concatenate([re, mre])
+    val = re[None, :] if im is None else np.stack([re, im])
+    return MtxMatrix(nrows, ncols, row, col, np.ascontiguousarray(val), field, sym)

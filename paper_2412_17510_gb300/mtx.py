@@ -88,26 +88,23 @@ def read_mtx(src):
     if len(entries) != nnz:
         raise ValueError("size line announces %d entries, file holds %d" % (nnz, len(entries)))
     width = {"pattern": 2, "real": 3, "integer": 3, "complex": 4}[field]
-    tab = np.zeros((nnz, width))
-    for k, ln in enumerate(entries):
-        t = ln.split()
-        if len(t) != width:
-            raise ValueError("entry %d: expected %d fields, got %d" % (k + 1, width, len(t)))
-        tab[k, :2] = (int(t[0]), int(t[1]))
-        if field == "integer":
-            tab[k, 2] = float(int(t[2]))
-        elif width > 2:
-            tab[k, 2:] = [float(v) for v in t[2:]]
-    row = tab[:, 0].astype(np.int64) - 1
-    col = tab[:, 1].astype(np.int64) - 1
+    counts = np.fromiter((len(ln.split()) for ln in entries), dtype=np.int64, count=nnz)
+    if nnz and (counts != width).any():
+        k = int(np.argmax(counts != width))
+        raise ValueError("entry %d: expected %d fields, got %d" % (k + 1, width, int(counts[k])))
+    tok = " ".join(entries).split()
+    ij = np.array(tok[0::width] + tok[1::width], dtype=np.int64).reshape(2, nnz) if nnz else np.zeros((2, 0), np.int64)
+    tab = np.array([tok[c::width] for c in range(2, width)], dtype=np.float64).reshape(width - 2, nnz)
+    row = ij[0] - 1
+    col = ij[1] - 1
     if nnz and (row.min() < 0 or col.min() < 0 or row.max() >= nrows or col.max() >= ncols):
         raise ValueError("index outside the stated shape")
     if field == "pattern":
         re, im = np.ones(nnz), None
     elif field == "complex":
-        re, im = tab[:, 2].copy(), tab[:, 3].copy()
+        re, im = tab[0].copy(), tab[1].copy()
     else:
-        re, im = tab[:, 2].copy(), None
+        re, im = tab[0].copy(), None
     if sym != "general":
         off = row != col
         if sym == "skew-symmetric" and (~off).any() and (re[~off] != 0).any():

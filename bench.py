@@ -224,6 +224,56 @@ def cpu_rate_for_step(rates, nnz_of):
     return tot_nnz / tot_t
 
 
+def sample_rows(coo, n=96, seed=17):
+    """Rows whose results the parity report checks: n random rows plus the
+    first, the last and the longest (so the bound's m is the matrix's own)."""
+    counts = np.bincount(coo.row, minlength=coo.nrows)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(coo.nrows, min(n, coo.nrows), replace=False)
+    return np.unique(np.concatenate([pick, [0, coo.nrows - 1, int(np.argmax(counts))]])).astype(np.int64)
+
+
+def parity_report(mats, xs_host, rows_of, ysamp, chunk_of):
+    """Error of the step's results on sampled rows (part of the oracle leg):
+    per arithmetic and variant, max |y - y_exact| / (8 m u (|A||x|)) over the
+    sampled components against the exact value, and whether the paper-order
+    rows that one run holds equal the oracle's row sums bit for bit.
+    ysamp[(arith, matrix, L)] holds the sampled columns of y (L x rows)."""
+    import oracle
+    from oracle import exact
+    out = {"rows_per_matrix": {m: int(len(r)) for m, r in rows_of.items()}, "max_bound_ratio": {},
+           "paper_one_run_rows_bit_identical": None, "paper_one_run_rows": 0}
+    bit_ok = True
+    for mname, coo in mats.items():
+        rows = rows_of[mname]
+        counts = np.bincount(coo.row, minlength=coo.nrows)
+        ip = np.zeros(coo.nrows + 1, dtype=np.int64)
+        np.cumsum(counts, out=ip[1:])
+        mask = np.isin(coo.row, rows, kind="table")
+        sub = workloads.COO(len(rows), coo.ncols, np.searchsorted(rows, coo.row[mask]), coo.col[mask],
+                            coo.val[:, mask])
+        for L in PRECS:
+            keys = [k for k in ysamp if k[1] == mname and k[2] == L]
+            if not keys:
+                continue
+            A = oracle.coo_to_csr(sub.nrows, sub.ncols, sub.row, sub.col, sub.promoted(L), L)
+            x = xs_host[mname][L]
+            ref = None
+            for key in keys:
+                y = ysamp[key]
+                out["max_bound_ratio"].setdefault(key[0], {})["%s/%s" % (mname, PNAME[L])] = \
+                    exact.bound_ratio(y, A, x)
+                if key[0] == "paper":
+                    K = chunk_of[key]
+                    one = (ip[rows] // K == (ip[rows + 1] - 1) // K) & (ip[rows + 1] > ip[rows])
+                    ref = oracle.spmv(A, x) if ref is None else ref
+                    bit_ok = bit_ok and bool(np.array_equal(y[:, one], ref[:, one]))
+                    out["paper_one_run_rows"] += int(one.sum())
+    if any(k[0] == "paper" for k in ysamp):
+        out["paper_one_run_rows_bit_identical"] = bit_ok
+    return out
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the oracle timed as it stands
 # ---------------------------------------------------------------------------
@@ -716,8 +766,31 @@ def main():
         other_out[ar] = {"value": onnz / (oms * 1e-3) / 1e9, "ms_per_step": oms,
                          "breakdown": breakdown_of(sets[ar], pv)}
 
+    # sampled rows of every variant's result, for the parity report of the
+    # oracle leg (one more product per variant, outside the timed region)
+    parity = None
+    samples = None
+    if pool is not None:
+        try:
+            rows_of = {m: sample_rows(c) for m, c in mats.items()}
+            samples, chunk_of = {}, {}
+            for ar in ariths:
+                for w in sets[ar]:
+                    mps.mpspmv_spmv(w["h"], w["x"], w["y"], stream)
+                    idx = torch.from_numpy(rows_of[w["m"]]).to(w["y"].device)
+                    samples[(ar, w["m"], w["L"])] = w["y"].index_select(1, idx).cpu().numpy()
+                    chunk_of[(ar, w["m"], w["L"])] = w["info"]["chunk"]
+            torch.cuda.synchronize()
+        except Exception as e:  # the report is diagnostic: it never stops the measurement
+            samples, parity = None, {"error": repr(e)}
+
     cpu = None
     if pool is not None:
+        if samples is not None:
+            try:
+                parity = parity_report(mats, xs_host, rows_of, samples, chunk_of)
+            except Exception as e:
+                parity = {"error": repr(e)}
         nnz_of = {(w["m"], w["L"]): w["nnz"] for w in variants}
         sample = {2: 4000000, 3: 500000, 4: 500000}
         t0 = time.perf_counter()
@@ -758,6 +831,8 @@ def main():
         }
         if other_out:
             line["other_arith"] = other_out
+        if parity is not None:
+            line["parity"] = parity
         if suite is not None:
             line["suite"] = suite
         print(json.dumps(line))

@@ -1,0 +1,65 @@
+"""The parity report of bench.py's oracle leg (host logic, no GPU): the
+sampled rows include the longest one, results that equal the oracle's give
+bit identity and ratios within the bound, and a perturbed result is caught."""
+import importlib.util
+import os
+
+import numpy as np
+
+import oracle
+import workloads
+from oracle import exact
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _setup(bench):
+    mats = {"stencil": workloads.stencil_27pt(6), "powerlaw": workloads.power_law(400, seed=3)}
+    xs = {m: {L: workloads.full_limb_vector(c.ncols, L, seed=0) for L in bench.PRECS} for m, c in mats.items()}
+    rows_of = {m: bench.sample_rows(c, n=40) for m, c in mats.items()}
+    ysamp, chunk_of = {}, {}
+    for m, c in mats.items():
+        rows = rows_of[m]
+        counts = np.bincount(c.row, minlength=c.nrows)
+        assert int(np.argmax(counts)) in rows and 0 in rows and c.nrows - 1 in rows
+        for L in bench.PRECS:
+            A = oracle.coo_to_csr(c.nrows, c.ncols, c.row, c.col, c.promoted(L), L)
+            ysamp[("paper", m, L)] = oracle.spmv(A, xs[m][L])[:, rows]
+            ysamp[("exact", m, L)] = exact.exact_round_rows(A, xs[m][L], rows)
+            chunk_of[("paper", m, L)] = chunk_of[("exact", m, L)] = 64
+    return mats, xs, rows_of, ysamp, chunk_of
+
+
+def test_parity_report_accepts_oracle_results():
+    bench = _bench()
+    mats, xs, rows_of, ysamp, chunk_of = _setup(bench)
+    rep = bench.parity_report(mats, xs, rows_of, ysamp, chunk_of)
+    assert rep["paper_one_run_rows_bit_identical"] is True and rep["paper_one_run_rows"] > 0
+    for ar in ("paper", "exact"):
+        assert len(rep["max_bound_ratio"][ar]) == 6
+        assert all(0.0 <= r <= 1.0 for r in rep["max_bound_ratio"][ar].values())
+
+
+def test_parity_report_catches_a_wrong_result():
+    bench = _bench()
+    mats, xs, rows_of, ysamp, chunk_of = _setup(bench)
+    rep0 = bench.parity_report(mats, xs, rows_of, ysamp, chunk_of)
+    # one ulp in the second component of every sampled stencil row (most of
+    # them lie inside one run of 64 entries), a relative 2^-30 in a QD result
+    y = ysamp[("paper", "stencil", 2)].copy()
+    y[1] = np.nextafter(y[1], np.inf)
+    ysamp[("paper", "stencil", 2)] = y
+    y = ysamp[("exact", "powerlaw", 4)].copy()
+    y[0] *= 1.0 + 2.0 ** -30
+    ysamp[("exact", "powerlaw", 4)] = y
+    rep = bench.parity_report(mats, xs, rows_of, ysamp, chunk_of)
+    assert rep["paper_one_run_rows_bit_identical"] is False
+    assert rep["max_bound_ratio"]["exact"]["powerlaw/QD"] > 1.0
+    assert rep["max_bound_ratio"]["exact"]["stencil/DD"] == rep0["max_bound_ratio"]["exact"]["stencil/DD"]

@@ -393,3 +393,37 @@ def test_flush_of_random_digit_arrays(lib, L):
         assert shift >= 0
         want = _cut(V << shift, L)
         assert np.array_equal(out, want), (L, case)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_shared_digit_accumulator_bound_over_the_whole_exponent_range(lib, L):
+    """Terms and products anywhere in the binary64 range (subnormal operands
+    included), so the window moves often and small terms fall below it.  The
+    dropped parts are below the window, whose lower end stays within
+    32 (D - 2) bits of the largest term's top bit, so the result is within
+    n 2^(T - 32 (D - 2) + 1) of the exact sum (T: the largest term's top bit)
+    plus one unit of its last component."""
+    rng = np.random.default_rng(500 + L)
+    D = DIGITS[L]
+    for case in range(400):
+        n = int(rng.integers(1, 60))
+        kind = (rng.random(n) < 0.5).astype(np.int32)
+        a = rng.standard_normal(n) * 2.0 ** rng.integers(-1070, 1000, n).astype(np.float64)
+        b = np.where(kind == 1, rng.standard_normal(n) * 2.0 ** rng.integers(-1070, 20, n).astype(np.float64), 0.0)
+        sub = rng.random(n) < 0.1
+        a[sub] = rng.integers(1, 1 << 40, int(sub.sum())) * 5e-324
+        neg = (rng.random(n) < 0.5).astype(np.int32)
+        terms = [_term(k, x, y, g) for k, x, y, g in zip(kind, a, b, neg)]
+        if any(not math.isfinite(x * y) for k, x, y in zip(kind, a, b) if k == 1):
+            continue
+        got = _fas(lib, L, kind, a, b, neg)
+        V = sum(terms)
+        T = max((abs(t).bit_length() - 1 for t in terms if t), default=0)
+        if V and abs(V).bit_length() - 1 - SC > 1023:
+            continue  # beyond the binary64 range: components overflow
+        top_v = abs(V).bit_length() - 1 if V else 0
+        bound = n * (1 << max(T - 32 * (D - 2) + 1, 0)) + (1 << max(top_v - 53 * L + 2, 0))
+        err = abs(sum(exact.f2i(c) for c in got) * (1 << exact.SCALE) - V)
+        # components below 2^-1074 are rounded by the conversion, not truncated
+        tiny = 1 << (SC - 1074 + 1)
+        assert err <= bound + L * tiny, (L, case, err, bound)

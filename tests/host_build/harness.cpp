@@ -110,6 +110,27 @@ int entry_sum(int mode, const double* a, const double* x, double* out) {
   return 0;
 }
 
+// A whole row: the terms of n stored entries added in order into one
+// accumulator (as the row-per-thread and run kernels do for a row that one
+// thread sums), cut to L components.  A and X hold n groups of L components.
+template <int L>
+void row_sum(int mode, int n, const double* A, const double* X, double* out) {
+  constexpr int D = kD<L>;
+  unsigned long long dp[D], dn[D];
+  mpk::FixAccS<D, 1> acc;
+  acc.dp = dp;
+  acc.dn = dn;
+  mpk::fas_reset<D, 1>(acc);
+  for (int k = 0; k < n; k++) {
+    const mpk::mp<L> xm = load_mp<L>(X + (size_t)k * L);
+    if (mode == 0)
+      mpk::add_prod<mpk::FixAccS<D, 1>, L>(acc, load_mp<L>(A + (size_t)k * L), xm, false);
+    else
+      mpk::add_prod_d<mpk::FixAccS<D, 1>, L>(acc, A[(size_t)k * L], xm, false);
+  }
+  mpk::fas_to_mp<L, D, 1>(acc, out);
+}
+
 // The flush alone, on given digit arrays (D = the kernels' digit count for L).
 template <int L>
 void flush(const unsigned long long* dp_in, const unsigned long long* dn_in, int base, double* out) {
@@ -130,6 +151,16 @@ void flush(const unsigned long long* dp_in, const unsigned long long* dn_in, int
 }  // namespace
 
 extern "C" {
+
+int host_row_sum(int L, int mode, int n, const double* A, const double* X, double* out) {
+  switch (L) {
+    case 1: row_sum<1>(mode, n, A, X, out); return 0;
+    case 2: row_sum<2>(mode, n, A, X, out); return 0;
+    case 3: row_sum<3>(mode, n, A, X, out); return 0;
+    case 4: row_sum<4>(mode, n, A, X, out); return 0;
+    default: return -1;
+  }
+}
 
 int host_flush(int L, const unsigned long long* dp, const unsigned long long* dn, int base, double* out) {
   switch (L) {

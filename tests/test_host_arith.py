@@ -59,6 +59,7 @@ def lib(tmp_path_factory):
     h.host_entry_sum.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
     _up = ctypes.POINTER(ctypes.c_ulonglong)
     h.host_flush.argtypes = [ctypes.c_int, _up, _up, ctypes.c_int, _dp]
+    h.host_row_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
     DIGITS.update({L: h.host_acc_digits(L) for L in (1, 2, 3, 4)})
     return h
 
@@ -427,3 +428,53 @@ def test_shared_digit_accumulator_bound_over_the_whole_exponent_range(lib, L):
         # components below 2^-1074 are rounded by the conversion, not truncated
         tiny = 1 << (SC - 1074 + 1)
         assert err <= bound + L * tiny, (L, case, err, bound)
+
+
+
+def _entry_term_list(L, mode, a, x):
+    """The individual terms (integers, units 2^-2148) an entry adds, for the
+    window check."""
+    if mode == 1:
+        if L == 1:
+            return [exact.f2i(a[0] * x[0]) << exact.SCALE]
+        return [exact.f2i(a[0]) * exact.f2i(x[j]) for j in range(L - 1)] + [exact.f2i(a[0] * x[L - 1]) << exact.SCALE]
+    if L == 1:
+        p, e = oracle.two_prod(a[0], x[0])
+        return [exact.f2i(p) << exact.SCALE, exact.f2i(e) << exact.SCALE]
+    terms = [exact.f2i(a[i]) * exact.f2i(x[j]) for i in range(L) for j in range(L) if i + j < L - 1]
+    c = a[L - 1] * x[0]
+    for i in range(L - 2, -1, -1):
+        c = _rn_fma(a[i], x[L - 1 - i], c)
+    return terms + [exact.f2i(c) << exact.SCALE]
+
+
+@pytest.mark.parametrize("L,mode", [(2, 0), (3, 0), (4, 0), (1, 1), (2, 1), (3, 1), (4, 1)])
+def test_row_sums_equal_the_exact_model(lib, L, mode):
+    """Whole rows as one thread sums them (stencil-like lengths, N(0,1)
+    matrix values, full-limb x): the device code returns exactly the cut sum
+    of the entries' decomposed terms whenever all of them fit the window.
+    This is the model a row of the exact kernels follows.  (Binary64 sums of
+    binary64 products, L = 1 with an MP value, add TwoProd pairs whose 106
+    bits exceed the 4-digit window: their tails are cut, within the bound.)"""
+    rng = np.random.default_rng(600 + 10 * L + mode)
+    D = DIGITS[L]
+    g = 32 * (D - 2) + 1
+    checked = 0
+    for case in range(150):
+        n = int(rng.integers(1, 40))
+        if mode == 1:
+            A = np.zeros((n, L))
+            A[:, 0] = rng.standard_normal(n)
+        else:
+            A = workloads.full_limb_vector(n, L, seed=int(rng.integers(1 << 30))).T.copy()
+            A *= rng.standard_normal(n)[:, None]
+        X = workloads.full_limb_vector(n, L, seed=int(rng.integers(1 << 30))).T.copy()
+        terms = [t for k in range(n) for t in _entry_term_list(L, mode, A[k], X[k])]
+        if _span(terms) > g:
+            continue
+        out = np.zeros(L)
+        assert lib.host_row_sum(L, mode, n, _d(np.ascontiguousarray(A)), _d(np.ascontiguousarray(X)), _d(out)) == 0
+        want = _cut(sum(_entry_terms(L, mode, A[k], X[k]) for k in range(n)), L)
+        assert np.array_equal(out, want), (L, mode, case)
+        checked += 1
+    assert checked >= 100

@@ -1,0 +1,89 @@
+"""Exact model of the exact-accumulation path (host-side test helper):
+what the kernels of handles created with MPSPMV_EXACT_ACC compute for a row
+that one thread sums, written with Python integers.  Every term is an integer
+times 2^-2148; an entry a . x contributes the exact products a_i x_j below
+the format's unit roundoff plus one FMA chain (csrc/exact_prod.cuh); the row
+value is the exact sum of those terms cut to L components by truncation of
+its magnitude.  The accumulator is exact while its terms fit its window,
+32 (D - 2) + 1 bits below the largest term's top bit (csrc/fixacc.cuh), so
+comparisons use rows whose terms span at most that."""
+import math
+from fractions import Fraction
+
+import numpy as np
+
+import oracle
+from oracle import exact
+
+SC = 2 * exact.SCALE  # terms and products are integers times 2^-2148
+DIGITS = {1: 4, 2: 6, 3: 8, 4: 10}  # accumulator digits per L (csrc/exact_prod.cuh, AccDigits)
+
+
+def window_bits(L):
+    return 32 * (DIGITS[L] - 2) + 1
+
+
+def rn_fma(a, b, c):
+    """fl(a b + c) with one rounding (Fraction -> float rounds correctly)."""
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def term(kind, a, b, neg):
+    """kind 0: the binary64 a; kind 1: the exact product a b."""
+    v = exact.f2i(a) << exact.SCALE if kind == 0 else exact.f2i(a) * exact.f2i(b)
+    return -v if neg else v
+
+
+def entry_terms(L, mode, a, x):
+    """The terms one stored entry adds (mode 0: MP value a, mode 1: binary64
+    value a[0]): exact products a_i x_j for i + j < L - 1 (a x_j for j < L - 1)
+    and the FMA chain over i + j = L - 1 (the rounded a x_{L-1}); L = 1 with
+    an MP value: the TwoProd pair."""
+    if mode == 1:
+        if L == 1:
+            return [exact.f2i(a[0] * x[0]) << exact.SCALE]
+        return [exact.f2i(a[0]) * exact.f2i(x[j]) for j in range(L - 1)] + [exact.f2i(a[0] * x[L - 1]) << exact.SCALE]
+    if L == 1:
+        p, e = oracle.two_prod(a[0], x[0])
+        return [exact.f2i(p) << exact.SCALE, exact.f2i(e) << exact.SCALE]
+    terms = [exact.f2i(a[i]) * exact.f2i(x[j]) for i in range(L) for j in range(L) if i + j < L - 1]
+    c = a[L - 1] * x[0]
+    for i in range(L - 2, -1, -1):
+        c = rn_fma(a[i], x[L - 1 - i], c)
+    return terms + [exact.f2i(c) << exact.SCALE]
+
+
+def cut(V, L):
+    """V * 2^-2148 cut to L components by truncation of its magnitude."""
+    out = np.zeros(L)
+    if V == 0:
+        return out
+    s = -1.0 if V < 0 else 1.0
+    m = abs(V)
+    top = m.bit_length() - 1
+    for l in range(L):
+        lsb = top - 52 - 53 * l
+        chunk = (m >> lsb) & ((1 << 53) - 1) if lsb >= 0 else (m << -lsb) & ((1 << 53) - 1)
+        out[l] = s * math.ldexp(chunk, lsb - SC)
+    return out
+
+
+def span(terms):
+    """Bits from the lowest set bit of any term to the top bit of the largest."""
+    nz = [abs(t) for t in terms if t]
+    if not nz:
+        return 0
+    lo = min((t & -t).bit_length() - 1 for t in nz)
+    hi = max(t.bit_length() - 1 for t in nz)
+    return hi - lo + 1
+
+
+def row_model(L, mode, A, x, r):
+    """(cut value, fits) of row r of the oracle CSR A (real) against x
+    (L x ncols): the exact model of the row and whether its terms fit the
+    window."""
+    terms = []
+    for k in range(A.indptr[r], A.indptr[r + 1]):
+        a = A.data[:L, k] if mode == 0 else A.data[:1, k]
+        terms += entry_terms(L, mode, a, x[:, int(A.indices[k])])
+    return cut(sum(terms), L), span(terms) <= window_bits(L)

@@ -8,6 +8,7 @@ import pytest
 import oracle
 import workloads
 from oracle import exact
+from tests import _exact_model as model
 from tests._util import csr_pair, gpu_spmv, to_dev, unsplit_rows
 
 pytestmark = pytest.mark.gpu
@@ -238,3 +239,44 @@ def test_row_per_thread_copy_matches_runs(L, cplx):
         assert (d <= 1e-12 * np.abs(Y[0]) + 1e-300).all()
     finally:
         mps.mpspmv_destroy(h)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("layout", ["rows", "runs"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rows_bit_identical_to_the_exact_model(L, layout, mode):
+    """Rows that one thread sums end to end equal the exact model bit for bit
+    (tests/_exact_model.py): the exact sum of the entries' decomposed terms
+    (exact products below the unit roundoff plus one FMA chain), cut to L
+    components by truncation -- for every row whose terms fit the window.
+    Layouts: the row-per-thread copy of a 27-point stencil (every row) and
+    the run layout of short random rows (the rows inside one run).  Values:
+    MP (every component random, mode 0) or binary64 (leading component
+    stored, mode 1)."""
+    coo = workloads.stencil_27pt(12) if layout == "rows" else workloads.random_sparse(3000, 3000, 6, seed=40 + L)
+    if mode == 0:
+        vals, limbs = workloads.full_limb_vector(coo.nnz, L, seed=50 + L), L
+        A = oracle.coo_to_csr(coo.nrows, coo.ncols, coo.row, coo.col, vals, L)
+    else:
+        vals, limbs = coo.val, 1
+        A = oracle.coo_to_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.promoted(L), L)
+    h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, vals, L, EX, val_limbs=limbs)
+    try:
+        info = mps.mpspmv_get_info(h)
+        x = workloads.full_limb_vector(coo.ncols, L, seed=60 + L)
+        y = gpu_spmv(h, x, L, coo.nrows)
+    finally:
+        mps.mpspmv_destroy(h)
+    if layout == "rows":
+        assert info["sell_slots"] > 0
+        rows = np.arange(coo.nrows)
+    else:
+        assert info["sell_slots"] == 0
+        rows = unsplit_rows(A, info["chunk"])
+    compared = 0
+    for r in rows:
+        want, fits = model.row_model(L, mode, A, x, int(r))
+        if fits:
+            assert np.array_equal(y[:, r], want), (L, layout, mode, int(r), y[:, r], want)
+            compared += 1
+    assert compared >= max(100, len(rows) // 2)

@@ -31,10 +31,20 @@ import pytest
 import oracle
 import workloads
 from oracle import exact
+from tests import _exact_model as model
+from tests._exact_model import SC
+from tests._exact_model import cut as _cut
+from tests._exact_model import entry_terms as _entry_term_list
+from tests._exact_model import rn_fma as _rn_fma  # noqa: F401
+from tests._exact_model import span as _span
+from tests._exact_model import term as _term
+
+
+def _entry_terms(L, mode, a, x):
+    return sum(_entry_term_list(L, mode, a, x))
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2412_17510_gb300", "csrc")
-SC = 2 * exact.SCALE  # terms and products are integers times 2^-2148
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -61,6 +71,7 @@ def lib(tmp_path_factory):
     h.host_flush.argtypes = [ctypes.c_int, _up, _up, ctypes.c_int, _dp]
     h.host_row_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
     DIGITS.update({L: h.host_acc_digits(L) for L in (1, 2, 3, 4)})
+    assert DIGITS == model.DIGITS  # the model's table is the kernels' one
     return h
 
 
@@ -113,36 +124,6 @@ def test_mp_ops_bit_identical_to_oracle(lib, L, op):
 # --------------------------------------------------------------------------
 # exact accumulators against exact integer sums
 # --------------------------------------------------------------------------
-def _term(kind, a, b, neg):
-    v = exact.f2i(a) << exact.SCALE if kind == 0 else exact.f2i(a) * exact.f2i(b)
-    return -v if neg else v
-
-
-def _cut(V, L):
-    """V * 2^-2148 cut to L components by truncation of its magnitude."""
-    out = np.zeros(L)
-    if V == 0:
-        return out
-    s = -1.0 if V < 0 else 1.0
-    m = abs(V)
-    top = m.bit_length() - 1
-    for l in range(L):
-        lsb = top - 52 - 53 * l
-        chunk = (m >> lsb) & ((1 << 53) - 1) if lsb >= 0 else (m << -lsb) & ((1 << 53) - 1)
-        out[l] = s * math.ldexp(chunk, lsb - SC)
-    return out
-
-
-def _span(terms):
-    """Bits from the lowest set bit of any term to the top bit of the largest."""
-    nz = [abs(t) for t in terms if t]
-    if not nz:
-        return 0
-    lo = min((t & -t).bit_length() - 1 for t in nz)
-    hi = max(t.bit_length() - 1 for t in nz)
-    return hi - lo + 1
-
-
 def _fas(lib, L, kind, a, b, neg):
     n = len(kind)
     kind = np.ascontiguousarray(kind, dtype=np.int32)
@@ -273,29 +254,6 @@ def test_chunk_to_double(lib):
 # --------------------------------------------------------------------------
 # the terms of one stored entry (exact_prod.cuh)
 # --------------------------------------------------------------------------
-def _rn_fma(a, b, c):
-    return float(Fraction(a) * Fraction(b) + Fraction(c))
-
-
-def _entry_terms(L, mode, a, x):
-    """Exact integer value (units 2^-2148) of the terms the kernels add for
-    one entry: exact products a_i x_j for i + j < L - 1, plus the FMA chain
-    over i + j = L - 1 (L = 1: the exact product); binary64 a: exact a x_j for
-    j < L - 1 plus the rounded a x_{L-1}."""
-    if mode == 1:
-        if L == 1:
-            return exact.f2i(a[0] * x[0]) << exact.SCALE
-        v = sum(exact.f2i(a[0]) * exact.f2i(x[j]) for j in range(L - 1))
-        return v + (exact.f2i(a[0] * x[L - 1]) << exact.SCALE)
-    if L == 1:
-        return exact.f2i(a[0]) * exact.f2i(x[0])
-    v = sum(exact.f2i(a[i]) * exact.f2i(x[j]) for i in range(L) for j in range(L) if i + j < L - 1)
-    c = a[L - 1] * x[0]
-    for i in range(L - 2, -1, -1):
-        c = _rn_fma(a[i], x[L - 1 - i], c)
-    return v + (exact.f2i(c) << exact.SCALE)
-
-
 @pytest.mark.parametrize("L", [1, 2, 3, 4])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_entry_products_match_their_decomposition(lib, L, mode):
@@ -429,23 +387,6 @@ def test_shared_digit_accumulator_bound_over_the_whole_exponent_range(lib, L):
         tiny = 1 << (SC - 1074 + 1)
         assert err <= bound + L * tiny, (L, case, err, bound)
 
-
-
-def _entry_term_list(L, mode, a, x):
-    """The individual terms (integers, units 2^-2148) an entry adds, for the
-    window check."""
-    if mode == 1:
-        if L == 1:
-            return [exact.f2i(a[0] * x[0]) << exact.SCALE]
-        return [exact.f2i(a[0]) * exact.f2i(x[j]) for j in range(L - 1)] + [exact.f2i(a[0] * x[L - 1]) << exact.SCALE]
-    if L == 1:
-        p, e = oracle.two_prod(a[0], x[0])
-        return [exact.f2i(p) << exact.SCALE, exact.f2i(e) << exact.SCALE]
-    terms = [exact.f2i(a[i]) * exact.f2i(x[j]) for i in range(L) for j in range(L) if i + j < L - 1]
-    c = a[L - 1] * x[0]
-    for i in range(L - 2, -1, -1):
-        c = _rn_fma(a[i], x[L - 1 - i], c)
-    return terms + [exact.f2i(c) << exact.SCALE]
 
 
 @pytest.mark.parametrize("L,mode", [(2, 0), (3, 0), (4, 0), (1, 1), (2, 1), (3, 1), (4, 1)])

@@ -79,11 +79,25 @@ def span(terms):
 
 
 def row_model(L, mode, A, x, r):
-    """(cut value, fits) of row r of the oracle CSR A (real) against x
-    (L x ncols): the exact model of the row and whether its terms fit the
-    window."""
-    terms = []
+    """(cut value, fits) of row r of the oracle CSR A against x (P x ncols):
+    the exact model of the row (real: L components; complex: the real part's
+    L components, then the imaginary part's) and whether the terms of every
+    part fit the window.  Complex entries follow the kernels' pattern:
+    re += a_re x_re - a_im x_im, im += a_re x_im + a_im x_re."""
+    def part(k, p):  # components of plane group p (0 real, 1 imaginary) of entry k
+        return A.data[p * L:p * L + L, k] if mode == 0 else A.data[p * L:p * L + 1, k]
+    if not A.cplx:
+        terms = []
+        for k in range(A.indptr[r], A.indptr[r + 1]):
+            terms += entry_terms(L, mode, part(k, 0), x[:L, int(A.indices[k])])
+        return cut(sum(terms), L), span(terms) <= window_bits(L)
+    re, im = [], []
     for k in range(A.indptr[r], A.indptr[r + 1]):
-        a = A.data[:L, k] if mode == 0 else A.data[:1, k]
-        terms += entry_terms(L, mode, a, x[:, int(A.indices[k])])
-    return cut(sum(terms), L), span(terms) <= window_bits(L)
+        c = int(A.indices[k])
+        xr, xi = x[:L, c], x[L:2 * L, c]
+        re += entry_terms(L, mode, part(k, 0), xr)
+        re += [-t for t in entry_terms(L, mode, part(k, 1), xi)]
+        im += entry_terms(L, mode, part(k, 0), xi)
+        im += entry_terms(L, mode, part(k, 1), xr)
+    fits = span(re) <= window_bits(L) and span(im) <= window_bits(L)
+    return np.concatenate([cut(sum(re), L), cut(sum(im), L)]), fits

@@ -131,6 +131,42 @@ void row_sum(int mode, int n, const double* A, const double* X, double* out) {
   mpk::fas_to_mp<L, D, 1>(acc, out);
 }
 
+// A whole complex row, with the kernels' per-entry pattern for complex data
+// (run_body.cuh, compute_entry): re += a_re x_re, re -= a_im x_im,
+// im += a_re x_im, im += a_im x_re, each product in the decomposed form.
+template <int L>
+void row_sum_c(int mode, int n, const double* Ar, const double* Ai, const double* Xr, const double* Xi,
+               double* out_re, double* out_im) {
+  constexpr int D = kD<L>;
+  using Acc = mpk::FixAccS<D, 1>;
+  unsigned long long d[4][D];
+  Acc sr, si;
+  sr.dp = d[0];
+  sr.dn = d[1];
+  si.dp = d[2];
+  si.dn = d[3];
+  mpk::fas_reset<D, 1>(sr);
+  mpk::fas_reset<D, 1>(si);
+  for (int k = 0; k < n; k++) {
+    const mpk::mp<L> xr = load_mp<L>(Xr + (size_t)k * L), xi = load_mp<L>(Xi + (size_t)k * L);
+    if (mode == 0) {
+      const mpk::mp<L> ar = load_mp<L>(Ar + (size_t)k * L), ai = load_mp<L>(Ai + (size_t)k * L);
+      mpk::add_prod<Acc, L>(sr, ar, xr, false);
+      mpk::add_prod<Acc, L>(sr, ai, xi, true);
+      mpk::add_prod<Acc, L>(si, ar, xi, false);
+      mpk::add_prod<Acc, L>(si, ai, xr, false);
+    } else {
+      const double ar = Ar[(size_t)k * L], ai = Ai[(size_t)k * L];
+      mpk::add_prod_d<Acc, L>(sr, ar, xr, false);
+      mpk::add_prod_d<Acc, L>(sr, ai, xi, true);
+      mpk::add_prod_d<Acc, L>(si, ar, xi, false);
+      mpk::add_prod_d<Acc, L>(si, ai, xr, false);
+    }
+  }
+  mpk::fas_to_mp<L, D, 1>(sr, out_re);
+  mpk::fas_to_mp<L, D, 1>(si, out_im);
+}
+
 // The flush alone, on given digit arrays (D = the kernels' digit count for L).
 template <int L>
 void flush(const unsigned long long* dp_in, const unsigned long long* dn_in, int base, double* out) {
@@ -158,6 +194,17 @@ int host_row_sum(int L, int mode, int n, const double* A, const double* X, doubl
     case 2: row_sum<2>(mode, n, A, X, out); return 0;
     case 3: row_sum<3>(mode, n, A, X, out); return 0;
     case 4: row_sum<4>(mode, n, A, X, out); return 0;
+    default: return -1;
+  }
+}
+
+int host_row_sum_c(int L, int mode, int n, const double* Ar, const double* Ai, const double* Xr, const double* Xi,
+                   double* out_re, double* out_im) {
+  switch (L) {
+    case 1: row_sum_c<1>(mode, n, Ar, Ai, Xr, Xi, out_re, out_im); return 0;
+    case 2: row_sum_c<2>(mode, n, Ar, Ai, Xr, Xi, out_re, out_im); return 0;
+    case 3: row_sum_c<3>(mode, n, Ar, Ai, Xr, Xi, out_re, out_im); return 0;
+    case 4: row_sum_c<4>(mode, n, Ar, Ai, Xr, Xi, out_re, out_im); return 0;
     default: return -1;
   }
 }

@@ -241,30 +241,47 @@ def test_row_per_thread_copy_matches_runs(L, cplx):
         mps.mpspmv_destroy(h)
 
 
+def _model_case(L, layout, mode, cplx):
+    """Matrix, its oracle CSR and the values passed to the handle for one
+    case of the exact-model test."""
+    if layout == "rows":
+        coo = workloads.stencil_27pt(12)
+        if cplx:
+            im = np.random.default_rng(70 + L).standard_normal(coo.nnz)
+            coo = workloads.COO(coo.nrows, coo.ncols, coo.row, coo.col, np.stack([coo.val[0], im]))
+    else:
+        coo = workloads.random_sparse(3000, 3000, 6, seed=40 + L, cplx=cplx)
+    if mode == 0:
+        vals, limbs = workloads.full_limb_vector(coo.nnz, L, seed=50 + L, cplx=cplx), L
+        A = oracle.coo_to_csr(coo.nrows, coo.ncols, coo.row, coo.col, vals, L, cplx)
+    else:
+        vals, limbs = coo.val, 1
+        A = oracle.coo_to_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.promoted(L), L, cplx)
+    return coo, A, vals, limbs
+
+
 @pytest.mark.parametrize("L", [2, 3, 4])
 @pytest.mark.parametrize("layout", ["rows", "runs"])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_rows_bit_identical_to_the_exact_model(L, layout, mode):
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rows_bit_identical_to_the_exact_model(L, layout, mode, cplx):
     """Rows that one thread sums end to end equal the exact model bit for bit
     (tests/_exact_model.py): the exact sum of the entries' decomposed terms
-    (exact products below the unit roundoff plus one FMA chain), cut to L
-    components by truncation -- for every row whose terms fit the window.
-    Layouts: the row-per-thread copy of a 27-point stencil (every row) and
-    the run layout of short random rows (the rows inside one run).  Values:
-    MP (every component random, mode 0) or binary64 (leading component
-    stored, mode 1)."""
-    coo = workloads.stencil_27pt(12) if layout == "rows" else workloads.random_sparse(3000, 3000, 6, seed=40 + L)
-    if mode == 0:
-        vals, limbs = workloads.full_limb_vector(coo.nnz, L, seed=50 + L), L
-        A = oracle.coo_to_csr(coo.nrows, coo.ncols, coo.row, coo.col, vals, L)
-    else:
-        vals, limbs = coo.val, 1
-        A = oracle.coo_to_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.promoted(L), L)
-    h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, vals, L, EX, val_limbs=limbs)
+    (exact products below the unit roundoff plus one FMA chain; complex data
+    in the pattern re += a_re x_re - a_im x_im, im += a_re x_im + a_im x_re),
+    cut to L components by truncation -- for every row whose terms fit the
+    window.  Layouts: the row-per-thread copy of a 27-point stencil (every
+    row) and the run layout of short random rows (the rows inside one run).
+    Values: MP (every component random, mode 0) or binary64 (leading
+    component stored, mode 1)."""
+    coo, A, vals, limbs = _model_case(L, layout, mode, cplx)
+    P = 2 * L if cplx else L
+    h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, vals, L,
+                              EX | (mps.MPSPMV_COMPLEX if cplx else 0), val_limbs=limbs)
     try:
         info = mps.mpspmv_get_info(h)
-        x = workloads.full_limb_vector(coo.ncols, L, seed=60 + L)
-        y = gpu_spmv(h, x, L, coo.nrows)
+        x = workloads.full_limb_vector(coo.ncols, L, seed=60 + L, cplx=cplx)
+        y = gpu_spmv(h, x, P, coo.nrows)
     finally:
         mps.mpspmv_destroy(h)
     if layout == "rows":
@@ -277,6 +294,6 @@ def test_rows_bit_identical_to_the_exact_model(L, layout, mode):
     for r in rows:
         want, fits = model.row_model(L, mode, A, x, int(r))
         if fits:
-            assert np.array_equal(y[:, r], want), (L, layout, mode, int(r), y[:, r], want)
+            assert np.array_equal(y[:, r], want), (L, layout, mode, cplx, int(r), y[:, r], want)
             compared += 1
     assert compared >= max(100, len(rows) // 2)

@@ -70,6 +70,7 @@ def lib(tmp_path_factory):
     _up = ctypes.POINTER(ctypes.c_ulonglong)
     h.host_flush.argtypes = [ctypes.c_int, _up, _up, ctypes.c_int, _dp]
     h.host_row_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+    h.host_row_sum_c.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
     DIGITS.update({L: h.host_acc_digits(L) for L in (1, 2, 3, 4)})
     assert DIGITS == model.DIGITS  # the model's table is the kernels' one
     return h
@@ -419,3 +420,33 @@ def test_row_sums_equal_the_exact_model(lib, L, mode):
         assert np.array_equal(out, want), (L, mode, case)
         checked += 1
     assert checked >= 100
+
+
+
+@pytest.mark.parametrize("L,mode", [(2, 0), (3, 0), (4, 0), (2, 1), (3, 1), (4, 1)])
+def test_complex_row_sums_equal_the_exact_model(lib, L, mode):
+    """Complex rows in the kernels' per-entry pattern (re += a_re x_re -
+    a_im x_im, im += a_re x_im + a_im x_re) against the model's complex row
+    (tests/_exact_model.py), for rows whose terms fit the window."""
+    rng = np.random.default_rng(700 + 10 * L + mode)
+    checked = 0
+    for case in range(80):
+        n = int(rng.integers(1, 30))
+        if mode == 1:
+            data = np.zeros((2 * L, n))
+            data[0] = rng.standard_normal(n)
+            data[L] = rng.standard_normal(n)
+        else:
+            data = workloads.full_limb_vector(n, L, seed=int(rng.integers(1 << 30)), cplx=True)
+        x = workloads.full_limb_vector(n, L, seed=int(rng.integers(1 << 30)), cplx=True)
+        A = oracle.CSR(1, n, np.array([0, n]), np.arange(n), data, L, True)
+        want, fits = model.row_model(L, mode, A, x, 0)
+        if not fits:
+            continue
+        ore, oim = np.zeros(L), np.zeros(L)
+        c = np.ascontiguousarray
+        assert lib.host_row_sum_c(L, mode, n, _d(c(data[:L].T)), _d(c(data[L:].T)), _d(c(x[:L].T)),
+                                  _d(c(x[L:].T)), _d(ore), _d(oim)) == 0
+        assert np.array_equal(np.concatenate([ore, oim]), want), (L, mode, case)
+        checked += 1
+    assert checked >= 60

@@ -101,3 +101,20 @@ def row_model(L, mode, A, x, r):
         im += entry_terms(L, mode, part(k, 1), xr)
     fits = span(re) <= window_bits(L) and span(im) <= window_bits(L)
     return np.concatenate([cut(sum(re), L), cut(sum(im), L)]), fits
+
+
+def axpy_model(L, alpha_re, alpha_im, u, v, cplx):
+    """(cut value, fits) of one element of w = u + alpha v on an exact
+    handle (the vector kernels' form): u's components added exactly, the
+    products alpha v in the decomposed form (complex: re takes
+    a_re v_re - a_im v_im, im takes a_re v_im + a_im v_re), each part cut once.
+    u and v hold P components of the element."""
+    def limbs(w):
+        return [exact.f2i(c) << exact.SCALE for c in w]
+    re = limbs(u[:L]) + entry_terms(L, 0, alpha_re, v[:L])
+    if not cplx:
+        return cut(sum(re), L), span(re) <= window_bits(L)
+    re += [-t for t in entry_terms(L, 0, alpha_im, v[L:2 * L])]
+    im = limbs(u[L:2 * L]) + entry_terms(L, 0, alpha_re, v[L:2 * L]) + entry_terms(L, 0, alpha_im, v[:L])
+    fits = span(re) <= window_bits(L) and span(im) <= window_bits(L)
+    return np.concatenate([cut(sum(re), L), cut(sum(im), L)]), fits

@@ -167,6 +167,35 @@ void row_sum_c(int mode, int n, const double* Ar, const double* Ai, const double
   mpk::fas_to_mp<L, D, 1>(si, out_im);
 }
 
+// One element of w = u + alpha v in the vector kernels' form (x_lin in
+// krylov_impl.cuh): u's components, then the decomposed products, one
+// accumulator per part, each part cut once.  alpha, u, v, out: P components.
+template <int L>
+void axpy_elem(int cplx, const double* alpha, const double* u, const double* v, double* out) {
+  constexpr int D = kD<L>;
+  using Acc = mpk::FixAccS<D, 1>;
+  unsigned long long dp[D], dn[D];
+  Acc e;
+  e.dp = dp;
+  e.dn = dn;
+  const mpk::mp<L> ar = load_mp<L>(alpha), vr = load_mp<L>(v);
+  mpk::fas_reset<D, 1>(e);
+  for (int l = 0; l < L; l++) mpk::acc_add(e, u[l], false);
+  mpk::add_prod<Acc, L>(e, ar, vr, false);
+  if (cplx) {
+    const mpk::mp<L> ai = load_mp<L>(alpha + L), vi = load_mp<L>(v + L);
+    mpk::add_prod<Acc, L>(e, ai, vi, true);
+    mpk::fas_to_mp<L, D, 1>(e, out);
+    mpk::fas_reset<D, 1>(e);
+    for (int l = 0; l < L; l++) mpk::acc_add(e, u[L + l], false);
+    mpk::add_prod<Acc, L>(e, ar, vi, false);
+    mpk::add_prod<Acc, L>(e, ai, vr, false);
+    mpk::fas_to_mp<L, D, 1>(e, out + L);
+  } else {
+    mpk::fas_to_mp<L, D, 1>(e, out);
+  }
+}
+
 // The flush alone, on given digit arrays (D = the kernels' digit count for L).
 template <int L>
 void flush(const unsigned long long* dp_in, const unsigned long long* dn_in, int base, double* out) {
@@ -205,6 +234,16 @@ int host_row_sum_c(int L, int mode, int n, const double* Ar, const double* Ai, c
     case 2: row_sum_c<2>(mode, n, Ar, Ai, Xr, Xi, out_re, out_im); return 0;
     case 3: row_sum_c<3>(mode, n, Ar, Ai, Xr, Xi, out_re, out_im); return 0;
     case 4: row_sum_c<4>(mode, n, Ar, Ai, Xr, Xi, out_re, out_im); return 0;
+    default: return -1;
+  }
+}
+
+int host_axpy_elem(int L, int cplx, const double* alpha, const double* u, const double* v, double* out) {
+  switch (L) {
+    case 1: axpy_elem<1>(cplx, alpha, u, v, out); return 0;
+    case 2: axpy_elem<2>(cplx, alpha, u, v, out); return 0;
+    case 3: axpy_elem<3>(cplx, alpha, u, v, out); return 0;
+    case 4: axpy_elem<4>(cplx, alpha, u, v, out); return 0;
     default: return -1;
   }
 }

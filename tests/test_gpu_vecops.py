@@ -14,6 +14,7 @@ import pytest
 import oracle
 import workloads
 from oracle import exact
+from tests import _exact_model as model
 from tests._util import csr_pair, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -284,3 +285,33 @@ def test_bicgstab_exact_handle(L, cplx):
         assert rr <= 4 * rtol
     finally:
         mps.mpspmv_destroy(h)
+
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_axpy_exact_bit_identical_to_the_exact_model(L, cplx):
+    """w = u + alpha v on an exact handle equals the exact model element by
+    element (tests/_exact_model.py: u's components plus the decomposed
+    products alpha v, each part cut once by truncation), for every element
+    whose terms fit the accumulator's window."""
+    n = 3000 + 5
+    u = workloads.full_limb_vector(n, L, seed=80 + L, cplx=cplx)
+    v = workloads.full_limb_vector(n, L, seed=90 + L, cplx=cplx)
+    ar, ai = alpha_of(L, cplx, 99)
+    h = vec_handle(L, cplx, True)
+    try:
+        ud, vd = to_dev(u), to_dev(v)
+        wd = torch.full_like(ud, float("nan"))
+        mps.mpspmv_axpy(h, n, ar, ud, vd, wd, alpha_im=ai if cplx else None)
+        torch.cuda.synchronize()
+        w = wd.cpu().numpy()
+    finally:
+        mps.mpspmv_destroy(h)
+    compared = 0
+    for i in range(n):
+        want, fits = model.axpy_model(L, ar, ai, u[:, i], v[:, i], cplx)
+        if fits:
+            assert np.array_equal(w[:, i], want), (L, cplx, i, w[:, i], want)
+            compared += 1
+    assert compared >= n // 2

@@ -71,6 +71,7 @@ def lib(tmp_path_factory):
     h.host_flush.argtypes = [ctypes.c_int, _up, _up, ctypes.c_int, _dp]
     h.host_row_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
     h.host_row_sum_c.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    h.host_axpy_elem.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
     DIGITS.update({L: h.host_acc_digits(L) for L in (1, 2, 3, 4)})
     assert DIGITS == model.DIGITS  # the model's table is the kernels' one
     return h
@@ -450,3 +451,29 @@ def test_complex_row_sums_equal_the_exact_model(lib, L, mode):
         assert np.array_equal(np.concatenate([ore, oim]), want), (L, mode, case)
         checked += 1
     assert checked >= 60
+
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_axpy_elements_equal_the_exact_model(lib, L, cplx):
+    """Elements of w = u + alpha v in the vector kernels' form against the
+    model's axpy element (tests/_exact_model.py), whenever they fit the
+    window."""
+    n = 400
+    P = 2 * L if cplx else L
+    u = workloads.full_limb_vector(n, L, seed=80 + L, cplx=cplx)
+    v = workloads.full_limb_vector(n, L, seed=90 + L, cplx=cplx)
+    a = workloads.full_limb_vector(1, L, seed=99, cplx=cplx)[:, 0]
+    ar, ai = a[:L], (a[L:] if cplx else np.zeros(L))
+    checked = 0
+    for i in range(n):
+        want, fits = model.axpy_model(L, ar, ai, u[:, i], v[:, i], cplx)
+        if not fits:
+            continue
+        out = np.zeros(P)
+        c = np.ascontiguousarray
+        assert lib.host_axpy_elem(L, int(cplx), _d(c(a)), _d(c(u[:, i])), _d(c(v[:, i])), _d(out)) == 0
+        assert np.array_equal(out, want), (L, cplx, i)
+        checked += 1
+    assert checked >= n // 2

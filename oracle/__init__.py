@@ -12,6 +12,9 @@ Layers:
   * ``exact``: the exact dyadic value of every SpMV row (big integers), the
     greedy rounding of an exact value to L components, and the componentwise
     error bound used as the acceptance test.
+  * ``exact_model``: the exact model of the exact-accumulation arithmetic
+    (MPSPMV_EXACT_ACC): the terms an entry contributes and their exact sum cut
+    to L components by truncation, for the bit-exact checks of that path.
   * ``mpref``: an independent 600-bit cross-check through mpmath (optional).
 
 Vectors and matrix values are structure-of-limbs float64 arrays of shape

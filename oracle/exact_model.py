@@ -1,22 +1,28 @@
-"""Exact model of the exact-accumulation path (host-side test helper):
-what the kernels of handles created with MPSPMV_EXACT_ACC compute for a row
-that one thread sums, written with Python integers.  Every term is an integer
-times 2^-2148; an entry a . x contributes the exact products a_i x_j below
-the format's unit roundoff plus one FMA chain (csrc/exact_prod.cuh); the row
-value is the exact sum of those terms cut to L components by truncation of
-its magnitude.  The accumulator is exact while its terms fit its window,
-32 (D - 2) + 1 bits below the largest term's top bit (csrc/fixacc.cuh), so
-comparisons use rows whose terms span at most that."""
+"""Exact model of the exact-accumulation arithmetic (MPSPMV_EXACT_ACC), for
+the parity checks of that path (test infrastructure, like the rest of this
+package: only tests/, smoke() and bench.py's oracle leg use it).
+
+The variant is defined by its terms, not by the paper's operation sequence:
+every term is an integer times 2^-2148 (binary64 values are integers times
+2^-1074); a stored entry a . x contributes the exact products a_i x_j below
+the format's unit roundoff plus one FMA chain over the next order (for a
+binary64 value a: the exact a x_j for j < L - 1 plus the rounded a x_{L-1});
+a row (or a vector update u + alpha v) is the exact sum of its terms, cut to
+L binary64 components by truncation of its magnitude.  The accumulator that
+computes it keeps D digits of 32 bits and is exact while the terms span at
+most 32 (D - 2) + 1 bits; comparisons use rows and elements within that
+span.  Written with Python integers, independently of the CUDA sources.
+"""
 import math
 from fractions import Fraction
 
 import numpy as np
 
-import oracle
-from oracle import exact
+from . import exact
+from . import two_prod as _two_prod
 
 SC = 2 * exact.SCALE  # terms and products are integers times 2^-2148
-DIGITS = {1: 4, 2: 6, 3: 8, 4: 10}  # accumulator digits per L (csrc/exact_prod.cuh, AccDigits)
+DIGITS = {1: 4, 2: 6, 3: 8, 4: 10}  # accumulator digits per L (binary64, DD, TD, QD)
 
 
 def window_bits(L):
@@ -44,7 +50,7 @@ def entry_terms(L, mode, a, x):
             return [exact.f2i(a[0] * x[0]) << exact.SCALE]
         return [exact.f2i(a[0]) * exact.f2i(x[j]) for j in range(L - 1)] + [exact.f2i(a[0] * x[L - 1]) << exact.SCALE]
     if L == 1:
-        p, e = oracle.two_prod(a[0], x[0])
+        p, e = _two_prod(a[0], x[0])
         return [exact.f2i(p) << exact.SCALE, exact.f2i(e) << exact.SCALE]
     terms = [exact.f2i(a[i]) * exact.f2i(x[j]) for i in range(L) for j in range(L) if i + j < L - 1]
     c = a[L - 1] * x[0]

@@ -8,7 +8,7 @@ import pytest
 import oracle
 import workloads
 from oracle import exact
-from tests import _exact_model as model
+from oracle import exact_model as model
 from tests._util import csr_pair, gpu_spmv, to_dev, unsplit_rows
 
 pytestmark = pytest.mark.gpu
@@ -266,7 +266,7 @@ def _model_case(L, layout, mode, cplx):
 @pytest.mark.parametrize("cplx", [False, True])
 def test_rows_bit_identical_to_the_exact_model(L, layout, mode, cplx):
     """Rows that one thread sums end to end equal the exact model bit for bit
-    (tests/_exact_model.py): the exact sum of the entries' decomposed terms
+    (oracle/exact_model.py): the exact sum of the entries' decomposed terms
     (exact products below the unit roundoff plus one FMA chain; complex data
     in the pattern re += a_re x_re - a_im x_im, im += a_re x_im + a_im x_re),
     cut to L components by truncation -- for every row whose terms fit the

@@ -14,7 +14,7 @@ import pytest
 import oracle
 import workloads
 from oracle import exact
-from tests import _exact_model as model
+from oracle import exact_model as model
 from tests._util import csr_pair, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -292,7 +292,7 @@ def test_bicgstab_exact_handle(L, cplx):
 @pytest.mark.parametrize("cplx", [False, True])
 def test_axpy_exact_bit_identical_to_the_exact_model(L, cplx):
     """w = u + alpha v on an exact handle equals the exact model element by
-    element (tests/_exact_model.py: u's components plus the decomposed
+    element (oracle/exact_model.py: u's components plus the decomposed
     products alpha v, each part cut once by truncation), for every element
     whose terms fit the accumulator's window."""
     n = 3000 + 5

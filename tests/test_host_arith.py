@@ -31,13 +31,13 @@ import pytest
 import oracle
 import workloads
 from oracle import exact
-from tests import _exact_model as model
-from tests._exact_model import SC
-from tests._exact_model import cut as _cut
-from tests._exact_model import entry_terms as _entry_term_list
-from tests._exact_model import rn_fma as _rn_fma  # noqa: F401
-from tests._exact_model import span as _span
-from tests._exact_model import term as _term
+from oracle import exact_model as model
+from oracle.exact_model import SC
+from oracle.exact_model import cut as _cut
+from oracle.exact_model import entry_terms as _entry_term_list
+from oracle.exact_model import rn_fma as _rn_fma  # noqa: F401
+from oracle.exact_model import span as _span
+from oracle.exact_model import term as _term
 
 
 def _entry_terms(L, mode, a, x):
@@ -428,7 +428,7 @@ def test_row_sums_equal_the_exact_model(lib, L, mode):
 def test_complex_row_sums_equal_the_exact_model(lib, L, mode):
     """Complex rows in the kernels' per-entry pattern (re += a_re x_re -
     a_im x_im, im += a_re x_im + a_im x_re) against the model's complex row
-    (tests/_exact_model.py), for rows whose terms fit the window."""
+    (oracle/exact_model.py), for rows whose terms fit the window."""
     rng = np.random.default_rng(700 + 10 * L + mode)
     checked = 0
     for case in range(80):
@@ -458,7 +458,7 @@ def test_complex_row_sums_equal_the_exact_model(lib, L, mode):
 @pytest.mark.parametrize("cplx", [False, True])
 def test_axpy_elements_equal_the_exact_model(lib, L, cplx):
     """Elements of w = u + alpha v in the vector kernels' form against the
-    model's axpy element (tests/_exact_model.py), whenever they fit the
+    model's axpy element (oracle/exact_model.py), whenever they fit the
     window."""
     n = 400
     P = 2 * L if cplx else L

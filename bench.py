@@ -233,17 +233,24 @@ def sample_rows(coo, n=96, seed=17):
     return np.unique(np.concatenate([pick, [0, coo.nrows - 1, int(np.argmax(counts))]])).astype(np.int64)
 
 
-def parity_report(mats, xs_host, rows_of, ysamp, chunk_of):
+def parity_report(mats, xs_host, rows_of, ysamp, chunk_of, sell_of=None):
     """Error of the step's results on sampled rows (part of the oracle leg):
     per arithmetic and variant, max |y - y_exact| / (8 m u (|A||x|)) over the
-    sampled components against the exact value, and whether the paper-order
-    rows that one run holds equal the oracle's row sums bit for bit.
-    ysamp[(arith, matrix, L)] holds the sampled columns of y (L x rows)."""
+    sampled components against the exact value; whether the paper-order rows
+    that one run holds equal the oracle's row sums bit for bit; and whether
+    the exact-arithmetic rows that one thread sums (every row of a
+    row-per-thread copy, sell_of[key] true, else the rows inside one run)
+    equal the exact model of that arithmetic bit for bit, where their terms
+    fit its window.  ysamp[(arith, matrix, L)] holds the sampled columns of y
+    (L x rows); the matrices hold binary64 values."""
     import oracle
     from oracle import exact
+    from oracle import exact_model
     out = {"rows_per_matrix": {m: int(len(r)) for m, r in rows_of.items()}, "max_bound_ratio": {},
-           "paper_one_run_rows_bit_identical": None, "paper_one_run_rows": 0}
+           "paper_one_run_rows_bit_identical": None, "paper_one_run_rows": 0,
+           "exact_model_rows_bit_identical": None, "exact_model_rows": 0}
     bit_ok = True
+    model_ok = True
     for mname, coo in mats.items():
         rows = rows_of[mname]
         counts = np.bincount(coo.row, minlength=coo.nrows)
@@ -263,14 +270,23 @@ def parity_report(mats, xs_host, rows_of, ysamp, chunk_of):
                 y = ysamp[key]
                 out["max_bound_ratio"].setdefault(key[0], {})["%s/%s" % (mname, PNAME[L])] = \
                     exact.bound_ratio(y, A, x)
+                K = chunk_of[key]
+                one = (ip[rows] // K == (ip[rows + 1] - 1) // K) & (ip[rows + 1] > ip[rows])
                 if key[0] == "paper":
-                    K = chunk_of[key]
-                    one = (ip[rows] // K == (ip[rows + 1] - 1) // K) & (ip[rows + 1] > ip[rows])
                     ref = oracle.spmv(A, x) if ref is None else ref
                     bit_ok = bit_ok and bool(np.array_equal(y[:, one], ref[:, one]))
                     out["paper_one_run_rows"] += int(one.sum())
+                elif key[0] == "exact":
+                    whole = np.ones(len(rows), dtype=bool) if (sell_of or {}).get(key) else one
+                    for i in np.nonzero(whole)[0]:
+                        want, fits = exact_model.row_model(L, 1, A, x, int(i))
+                        if fits:
+                            model_ok = model_ok and bool(np.array_equal(y[:, i], want))
+                            out["exact_model_rows"] += 1
     if any(k[0] == "paper" for k in ysamp):
         out["paper_one_run_rows_bit_identical"] = bit_ok
+    if out["exact_model_rows"]:
+        out["exact_model_rows_bit_identical"] = model_ok
     return out
 
 
@@ -773,13 +789,14 @@ def main():
     if pool is not None:
         try:
             rows_of = {m: sample_rows(c) for m, c in mats.items()}
-            samples, chunk_of = {}, {}
+            samples, chunk_of, sell_of = {}, {}, {}
             for ar in ariths:
                 for w in sets[ar]:
                     mps.mpspmv_spmv(w["h"], w["x"], w["y"], stream)
                     idx = torch.from_numpy(rows_of[w["m"]]).to(w["y"].device)
                     samples[(ar, w["m"], w["L"])] = w["y"].index_select(1, idx).cpu().numpy()
                     chunk_of[(ar, w["m"], w["L"])] = w["info"]["chunk"]
+                    sell_of[(ar, w["m"], w["L"])] = w["info"]["sell_slots"] > 0
             torch.cuda.synchronize()
         except Exception as e:  # the report is diagnostic: it never stops the measurement
             samples, parity = None, {"error": repr(e)}
@@ -788,7 +805,7 @@ def main():
     if pool is not None:
         if samples is not None:
             try:
-                parity = parity_report(mats, xs_host, rows_of, samples, chunk_of)
+                parity = parity_report(mats, xs_host, rows_of, samples, chunk_of, sell_of)
             except Exception as e:
                 parity = {"error": repr(e)}
         nnz_of = {(w["m"], w["L"]): w["nnz"] for w in variants}

@@ -9,6 +9,7 @@ import numpy as np
 import oracle
 import workloads
 from oracle import exact
+from oracle import exact_model as em
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -32,7 +33,12 @@ def _setup(bench):
         for L in bench.PRECS:
             A = oracle.coo_to_csr(c.nrows, c.ncols, c.row, c.col, c.promoted(L), L)
             ysamp[("paper", m, L)] = oracle.spmv(A, xs[m][L])[:, rows]
-            ysamp[("exact", m, L)] = exact.exact_round_rows(A, xs[m][L], rows)
+            sub = oracle.CSR(len(rows), c.ncols, np.concatenate([[0], np.cumsum(np.diff(A.indptr)[rows])]),
+                             np.concatenate([A.indices[A.indptr[r]:A.indptr[r + 1]] for r in rows]),
+                             np.concatenate([A.data[:, A.indptr[r]:A.indptr[r + 1]] for r in rows], axis=1), L,
+                             False)
+            ysamp[("exact", m, L)] = np.stack([em.row_model(L, 1, sub, xs[m][L], i)[0] for i in range(len(rows))],
+                                              axis=1)
             chunk_of[("paper", m, L)] = chunk_of[("exact", m, L)] = 64
     return mats, xs, rows_of, ysamp, chunk_of
 
@@ -40,8 +46,10 @@ def _setup(bench):
 def test_parity_report_accepts_oracle_results():
     bench = _bench()
     mats, xs, rows_of, ysamp, chunk_of = _setup(bench)
-    rep = bench.parity_report(mats, xs, rows_of, ysamp, chunk_of)
+    sell_of = {k: k[1] == "stencil" for k in ysamp}
+    rep = bench.parity_report(mats, xs, rows_of, ysamp, chunk_of, sell_of)
     assert rep["paper_one_run_rows_bit_identical"] is True and rep["paper_one_run_rows"] > 0
+    assert rep["exact_model_rows_bit_identical"] is True and rep["exact_model_rows"] > 100
     for ar in ("paper", "exact"):
         assert len(rep["max_bound_ratio"][ar]) == 6
         assert all(0.0 <= r <= 1.0 for r in rep["max_bound_ratio"][ar].values())
@@ -59,7 +67,9 @@ def test_parity_report_catches_a_wrong_result():
     y = ysamp[("exact", "powerlaw", 4)].copy()
     y[0] *= 1.0 + 2.0 ** -30
     ysamp[("exact", "powerlaw", 4)] = y
-    rep = bench.parity_report(mats, xs, rows_of, ysamp, chunk_of)
+    sell_of = {k: k[1] == "stencil" for k in ysamp}
+    rep = bench.parity_report(mats, xs, rows_of, ysamp, chunk_of, sell_of)
     assert rep["paper_one_run_rows_bit_identical"] is False
+    assert rep["exact_model_rows_bit_identical"] is False
     assert rep["max_bound_ratio"]["exact"]["powerlaw/QD"] > 1.0
     assert rep["max_bound_ratio"]["exact"]["stencil/DD"] == rep0["max_bound_ratio"]["exact"]["stencil/DD"]

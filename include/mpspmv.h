@@ -167,6 +167,18 @@ int mpspmv_spmtv(mpspmv_h h, const double* x, double* y, void* stream);
 int mpspmv_spmv_host(mpspmv_h h, const double* x_host, double* y_host, void* stream);
 
 /*
+ * mpspmv_spmv_host_async -- mpspmv_spmv_host without the final
+ * synchronisation: the copy of x in, the product and the copy of y out are
+ * enqueued on `stream` and the call returns.  x_host and y_host must be
+ * pinned (page-locked) host memory and stay valid, unread (y) and unmodified
+ * (x), until `stream` has completed.  Products of different handles on
+ * different streams then overlap one product's copies with another's
+ * kernels.  Two calls on the same handle use the same device buffers: order
+ * them on one stream.
+ */
+int mpspmv_spmv_host_async(mpspmv_h h, const double* x_host, double* y_host, void* stream);
+
+/*
  * mpspmv_spmm -- Y = A X for k right-hand sides (1 <= k <= 32).
  *
  *  X  device, P planes; plane p, row j, column c at X[(p*ncols + j)*ldx + c]
@@ -257,6 +269,28 @@ int mpspmv_gpbicg(mpspmv_h h, const double* b, double* x, double rtol, double at
 int mpspmv_dot(mpspmv_h h, int64_t n, const double* u, const double* v, double* out, void* stream);
 int mpspmv_axpy(mpspmv_h h, int64_t n, const double* alpha, const double* u, const double* v, double* w,
                 void* stream);
+
+/*
+ * MP scalars of a solve whose vectors are split into row blocks, one block
+ * per process (the row-parallel CSR product of Section 3 with the inner
+ * products of Section 4.2's solvers).  The handle supplies L, real or
+ * complex, and the arithmetic only.  Scalars use mpspmv_dot's layout: 2L
+ * host doubles, the real part's components, then the imaginary part's.
+ *
+ * mpspmv_scalar_sum -- out = parts[0] + parts[1] + ... + parts[count-1]
+ *   (parts: host, count x 2L doubles, e.g. the blocks' mpspmv_dot results in
+ *   rank order; 1 <= count <= 4096).  Paper order: MP additions from left to
+ *   right, so every process that sums the same parts gets the same bits,
+ *   independent of any collective's own summation order.  MPSPMV_EXACT_ACC
+ *   handles: the exact sum of all components, cut to L components once.
+ * mpspmv_scalar_div -- out = a / b in the handle's precision (complex:
+ *   a conj(b) / |b|^2 after scaling a and b by one power of two).
+ *   MPSPMV_EBREAKDOWN when every component of b is zero.
+ * Both run one device thread and synchronise `stream`; MPSPMV_EINVAL for a
+ * NULL pointer or a count out of range.
+ */
+int mpspmv_scalar_sum(mpspmv_h h, int count, const double* parts, double* out, void* stream);
+int mpspmv_scalar_div(mpspmv_h h, const double* a, const double* b, double* out, void* stream);
 
 /*
  * Batched products and solves over many independent matrices of one
@@ -375,6 +409,22 @@ int mpspmv_mlp_train(float* params, int C, const float* X, const int* y, int n, 
                      float* loss_per_epoch, void* stream);
 
 /*
+ * Input standardisation of the selector network, on the device.
+ * mpspmv_mlp_standardize -- for n feature vectors X (device, n x 32
+ *   row-major): mu, sd (device, 32 floats each) = mean and population
+ *   standard deviation of every feature (binary64 sums in sample order,
+ *   rounded to float; a deviation below 1e-6 becomes 1), and Xs (device,
+ *   n x 32) = (X - mu) / sd.  Asynchronous.
+ * mpspmv_mlp_fold -- rewrite W1 and b1 of params (device) in place so that
+ *   the network takes raw features: W1 / sd (row i divided by sd_i) and
+ *   b1 - (mu / sd) W1, in binary64 rounded to float.  A network trained on
+ *   mpspmv_mlp_standardize's Xs then gives, on raw X, the logits it gave on Xs
+ *   (to float rounding).  Asynchronous.
+ */
+int mpspmv_mlp_standardize(const float* X, int n, float* mu, float* sd, float* Xs, void* stream);
+int mpspmv_mlp_fold(float* params, int C, const float* mu, const float* sd, void* stream);
+
+/*
  * mpspmv_select_precision -- features of (hs[0], b) (binary64 CG history
  * included) -> network -> *prec in 1..4 (classes binary64, DD, TD, QD and
  * "none", which maps to QD).  feat_out: host 32 floats, may be NULL.
@@ -392,12 +442,18 @@ int mpspmv_solve_auto(const mpspmv_h* hs, const float* params, int C, const doub
  * memory when they multiply: a process that has given all of its device
  * memory to its own pool or arena at start-up, or a latency-bound loop that
  * cannot take the device-wide synchronisation of cudaMalloc / cudaFree.  The
- * paper has no counterpart; the arithmetic is that of mpspmv_spmv (runs of 16
- * stored entries summed one per thread, Algorithms 1-2 / QD sloppy forms),
- * but the matrix comes as plain caller-owned CSR arrays and no handle is made.
+ * paper has no counterpart.  The matrix comes as plain caller-owned CSR
+ * arrays and no handle is made; the arithmetic is the paper-order MP
+ * multiply and add of mpspmv_spmv, over runs of 16 stored entries summed
+ * one per thread.  Results meet the bound of mpspmv_spmv,
+ * 8 m u (|A||x|)_i; they equal mpspmv_spmv's bit for bit only on rows that
+ * both entry points sum within one run (a handle cuts rows into runs of
+ * another length, and MPSPMV_EXACT_ACC handles use another arithmetic).
  *
  *  prec        1..4 (L).   flags  0 or MPSPMV_COMPLEX (P = L or 2L planes).
- *  nrows, ncols, nnz   shape; nnz = indptr[nrows] (not read from the device).
+ *  nrows, ncols, nnz   shape; nnz must equal indptr[nrows] (it is not read
+ *              from the device): with a smaller nnz, rows past the first nnz
+ *              entries are left unspecified, with no error.
  *  indptr      device, nrows + 1 int64 row offsets, non-decreasing from 0.
  *  indices     device, nnz int32 column indices, each in [0, ncols).
  *  vals        device, P planes of nnz binary64 (CSR order, structure of limbs).
@@ -405,15 +461,23 @@ int mpspmv_solve_auto(const mpspmv_h* hs, const float* params, int C, const doub
  *
  * No cudaMalloc, cudaFree or allocating library call is made.  The partial
  * sums of rows that cross a run boundary go to a fixed 32 MiB array in the
- * library's device image (every GPU that loads the library holds it until
- * the process exits), so nnz may be at most 2^22 / (2 P) * 16 (DD: 16,777,216;
- * QD complex: 4,194,304); larger problems return MPSPMV_EINVAL.  The first
- * call on a device looks up that array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture.  Every call
- * shares the array and leaves its partial sums there; each call writes every
- * slot it reads, so nothing needs clearing, but calls that overlap on the GPU
- * (two streams, or two host threads) race on it and must be ordered by the
- * caller.  Asynchronous on `stream`.
+ * library's device image, so nnz may be at most 2^22 / (2 P) * 16 (DD:
+ * 16,777,216; QD complex: 4,194,304); larger problems return MPSPMV_EINVAL.
+ *
+ * Set-up: CUDA loads the module that holds the array lazily, on the first
+ * call on each device; that call places the array (32 MiB, kept until the
+ * process exits) and the module's code in device memory, looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it.  A call with
+ * nrows = 0 (pointers may be NULL) does only this set-up.  Make one such call
+ * per device, with that device current, at start-up: before the caller's
+ * pool or arena claims the device's memory, and before any stream capture.
+ * The cached address belongs to the device's primary context: after
+ * cudaDeviceReset this entry point must not be used again in the process.
+ *
+ * Every call shares the array and leaves its partial sums there; each call
+ * writes every slot it reads, so nothing needs clearing, but calls that
+ * overlap on the GPU (two streams, or two host threads) race on it and must
+ * be ordered by the caller.  Asynchronous on `stream`.
  */
 int mpspmv_spmv_csr_noalloc(int prec, unsigned flags, int64_t nrows, int64_t ncols, int64_t nnz,
                             const int64_t* indptr, const int32_t* indices, const double* vals, const double* x,

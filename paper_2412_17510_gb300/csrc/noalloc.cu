@@ -31,7 +31,9 @@ std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in for it).
+// per device (the host-side symbol is only a stand-in for it).  The address
+// belongs to the device's primary context and is cached for the life of the
+// process: after cudaDeviceReset this entry point must not be called again.
 int scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -213,11 +215,14 @@ extern "C" int mpspmv_spmv_csr_noalloc(int prec, unsigned flags, int64_t nrows, 
   if (prec < 1 || prec > 4 || (flags & ~MPSPMV_COMPLEX) || nrows < 0 || ncols < 0 || nnz < 0) return MPSPMV_EINVAL;
   const bool cplx = flags & MPSPMV_COMPLEX;
   if (nnz > max_nnz(prec, cplx)) return MPSPMV_EINVAL;
-  if (nrows == 0) return MPSPMV_OK;
-  if (!indptr || !y || (nnz > 0 && (!indices || !vals || !x))) return MPSPMV_EINVAL;
+  // The set-up (loading this file's module, which places the scratch array
+  // on the device, and looking up its address) runs on the first call on a
+  // device, also for nrows == 0: such a call does only the set-up.
   double* carry = nullptr;
   int st = scratch_address(&carry);
   if (st != MPSPMV_OK) return st;
+  if (nrows == 0) return MPSPMV_OK;
+  if (!indptr || !y || (nnz > 0 && (!indices || !vals || !x))) return MPSPMV_EINVAL;
   cudaStream_t s = mps_stream(stream);
   switch (prec * 2 + (cplx ? 1 : 0)) {
     case 2: return run<1, false>(nrows, ncols, indptr, indices, vals, nnz, x, y, carry, s);

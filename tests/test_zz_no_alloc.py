@@ -73,6 +73,27 @@ def pair_ratio(y1, y2, A, x, rows):
     return worst
 
 
+def test_noalloc_setup_call_before_products():
+    """The documented start-up call: nrows = 0 with NULL pointers does only
+    the set-up (loads the module holding the scratch array, looks up its
+    address) and succeeds; a product right after it matches the handle
+    entry point on rows both sum within one run."""
+    mps.mpspmv_spmv_csr_noalloc(2, 0, 0, 0, 0, None, None, None, None, None)
+    mps.mpspmv_spmv_csr_noalloc(4, mps.MPSPMV_COMPLEX, 0, 0, 0, None, None, None, None, None)
+    coo = workloads.laplacian_2d(20)
+    A, h = csr_pair(coo, 2)
+    try:
+        x = workloads.full_limb_vector(coo.ncols, 2, seed=9)
+        y_na = run_noalloc(2, 0, coo, coo.promoted(2), x)
+        y_h = run_handle(h, x, 2, coo.nrows)
+        same, _ = same_runs(A, mps.mpspmv_get_info(h)["chunk"])
+        assert same.any()
+        assert np.array_equal(y_na[:, same], y_h[:, same])
+        assert exact.bound_ratio(y_na, A, x) <= 1.0
+    finally:
+        mps.mpspmv_destroy(h)
+
+
 @pytest.mark.parametrize("L", [2, 4])
 def test_noalloc_matches_handle_entry_point(L):
     """27-point stencil 32^3 (830,584 entries), full-limb x: two calls in a

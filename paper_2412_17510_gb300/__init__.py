@@ -60,6 +60,7 @@ def _load():
         "mpspmv_spmv": [vp, vp, vp, vp],
         "mpspmv_spmtv": [vp, vp, vp, vp],
         "mpspmv_spmv_host": [vp, vp, vp, vp],
+        "mpspmv_spmv_host_async": [vp, vp, vp, vp],
         "mpspmv_spmm": [vp, c_int, vp, i64, vp, i64, vp],
         "mpspmv_probe_fp64": [c_int, c_int, ctypes.POINTER(ctypes.c_double), vp],
         "mpspmv_cg": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
@@ -68,6 +69,8 @@ def _load():
                             ctypes.POINTER(ctypes.c_double), vp],
         "mpspmv_dot": [vp, i64, vp, vp, vp, vp],
         "mpspmv_axpy": [vp, i64, vp, vp, vp, vp, vp],
+        "mpspmv_scalar_sum": [vp, c_int, vp, vp, vp],
+        "mpspmv_scalar_div": [vp, vp, vp, vp, vp],
         "mpspmv_bicg": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
                         ctypes.POINTER(ctypes.c_double), vp],
         "mpspmv_cgs": [vp, vp, vp, ctypes.c_double, ctypes.c_double, c_int, ctypes.POINTER(c_int),
@@ -86,6 +89,8 @@ def _load():
         "mpspmv_mlp_forward": [vp, c_int, vp, c_int, vp, vp],
         "mpspmv_mlp_grad": [vp, c_int, vp, vp, c_int, vp, vp, vp],
         "mpspmv_mlp_train": [vp, c_int, vp, vp, c_int, c_int, c_int, ctypes.c_float, vp, vp],
+        "mpspmv_mlp_standardize": [vp, c_int, vp, vp, vp, vp],
+        "mpspmv_mlp_fold": [vp, c_int, vp, vp, vp],
         "mpspmv_select_precision": [vp, vp, c_int, vp, vp, vp, vp],
         "mpspmv_solve_auto": [vp, vp, c_int, vp, vp, ctypes.c_double, ctypes.c_double, c_int, vp, vp, vp, vp, vp],
     }
@@ -181,6 +186,12 @@ def mpspmv_spmv_host(h, x_host, y_host, stream=None):
     _check(_lib.mpspmv_spmv_host(h, _ptr(x_host), _ptr(y_host), _stream(stream)), "mpspmv_spmv_host")
 
 
+def mpspmv_spmv_host_async(h, x_host, y_host, stream=None):
+    """Enqueue x -> device, y = A x, y -> host on ``stream`` (pinned host
+    buffers, valid until the stream completes)."""
+    _check(_lib.mpspmv_spmv_host_async(h, _ptr(x_host), _ptr(y_host), _stream(stream)), "mpspmv_spmv_host_async")
+
+
 def mpspmv_spmm(h, k, X, ldx, Y, ldy, stream=None):
     _check(_lib.mpspmv_spmm(h, k, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)), "mpspmv_spmm")
 
@@ -239,6 +250,31 @@ def mpspmv_axpy(h, n, alpha_re, u, v, w, alpha_im=None, stream=None):
         ai = np.atleast_1d(np.asarray(alpha_im, dtype=np.float64))
         a[L:L + ai.size] = ai
     _check(_lib.mpspmv_axpy(h, n, a.ctypes.data, _ptr(u), _ptr(v), _ptr(w), _stream(stream)), "mpspmv_axpy")
+
+
+def mpspmv_scalar_sum(h, parts, stream=None):
+    """Sum of MP scalars in order; ``parts`` is (count, 2L) (each row a
+    scalar in mpspmv_dot's layout).  Returns (re, im) as two arrays of L
+    components."""
+    L = mpspmv_get_info(h)["prec"]
+    p = np.ascontiguousarray(np.atleast_2d(parts), dtype=np.float64)
+    if p.shape[1] != 2 * L:
+        raise ValueError("parts must have 2L columns")
+    out = np.zeros(2 * L)
+    _check(_lib.mpspmv_scalar_sum(h, p.shape[0], p.ctypes.data, out.ctypes.data, _stream(stream)),
+           "mpspmv_scalar_sum")
+    return out[:L].copy(), out[L:].copy()
+
+
+def mpspmv_scalar_div(h, a, b, stream=None):
+    """a / b for MP scalars of 2L components each; returns (re, im)."""
+    L = mpspmv_get_info(h)["prec"]
+    aa = np.ascontiguousarray(a, dtype=np.float64).reshape(2 * L)
+    bb = np.ascontiguousarray(b, dtype=np.float64).reshape(2 * L)
+    out = np.zeros(2 * L)
+    _check(_lib.mpspmv_scalar_div(h, aa.ctypes.data, bb.ctypes.data, out.ctypes.data, _stream(stream)),
+           "mpspmv_scalar_div")
+    return out[:L].copy(), out[L:].copy()
 
 
 def mpspmv_spmv_csr_noalloc(prec, flags, nrows, ncols, nnz, indptr, indices, vals, x, y, stream=None):
@@ -346,6 +382,17 @@ def mpspmv_mlp_train(params, C, X, y, n, batch, epochs, lr, stream=None):
     _check(_lib.mpspmv_mlp_train(_ptr(params), C, _ptr(X), _ptr(y), n, batch, epochs, ctypes.c_float(lr),
                                  losses.ctypes.data, _stream(stream)), "mpspmv_mlp_train")
     return losses[:epochs]
+
+
+def mpspmv_mlp_standardize(X, n, mu, sd, Xs, stream=None):
+    """Device arrays: mu, sd (32 floats) and Xs = (X - mu) / sd."""
+    _check(_lib.mpspmv_mlp_standardize(_ptr(X), n, _ptr(mu), _ptr(sd), _ptr(Xs), _stream(stream)),
+           "mpspmv_mlp_standardize")
+
+
+def mpspmv_mlp_fold(params, C, mu, sd, stream=None):
+    """Fold the standardisation (mu, sd: device) into W1, b1 of params in place."""
+    _check(_lib.mpspmv_mlp_fold(_ptr(params), C, _ptr(mu), _ptr(sd), _stream(stream)), "mpspmv_mlp_fold")
 
 
 def mpspmv_select_precision(hs, params, C, b, stream=None):

@@ -335,6 +335,29 @@ void mps_note_cuda_error(cudaError_t e, const char* what, const char* file, int 
   std::snprintf(g_last_cuda, sizeof(g_last_cuda), "%s (%s) at %s:%d", cudaGetErrorString(e), what, file, line);
 }
 
+namespace {
+
+// x (host) -> handle buffer, product, handle buffer -> y (host), enqueued on s
+int spmv_host_enqueue(mpspmv_h h, const double* x_host, double* y_host, cudaStream_t s) {
+  const int64_t xb = sizeof(double) * h->P * std::max<int64_t>(h->ncols, 1);
+  const int64_t yb = sizeof(double) * h->P * std::max<int64_t>(h->nrows, 1);
+  if (!h->d_xbuf) {
+    if (cudaMalloc(&h->d_xbuf, xb) != cudaSuccess) return MPSPMV_ENOMEM;
+    h->device_bytes += xb;
+  }
+  if (!h->d_ybuf) {
+    if (cudaMalloc(&h->d_ybuf, yb) != cudaSuccess) return MPSPMV_ENOMEM;
+    h->device_bytes += yb;
+  }
+  MPS_CUDA(cudaMemcpyAsync(h->d_xbuf, x_host, sizeof(double) * h->P * h->ncols, cudaMemcpyHostToDevice, s));
+  int st = mps_launch_spmv(h, h->d_xbuf, h->d_ybuf, s);
+  if (st != MPSPMV_OK) return st;
+  MPS_CUDA(cudaMemcpyAsync(y_host, h->d_ybuf, sizeof(double) * h->P * h->nrows, cudaMemcpyDeviceToHost, s));
+  return MPSPMV_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int mpspmv_create_csr(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz, const int64_t* row,
@@ -403,22 +426,15 @@ int mpspmv_spmtv(mpspmv_h h, const double* x, double* y, void* stream) {
 int mpspmv_spmv_host(mpspmv_h h, const double* x_host, double* y_host, void* stream) {
   if (!h || !x_host || !y_host) return MPSPMV_EINVAL;
   cudaStream_t s = mps_stream(stream);
-  const int64_t xb = sizeof(double) * h->P * std::max<int64_t>(h->ncols, 1);
-  const int64_t yb = sizeof(double) * h->P * std::max<int64_t>(h->nrows, 1);
-  if (!h->d_xbuf) {
-    if (cudaMalloc(&h->d_xbuf, xb) != cudaSuccess) return MPSPMV_ENOMEM;
-    h->device_bytes += xb;
-  }
-  if (!h->d_ybuf) {
-    if (cudaMalloc(&h->d_ybuf, yb) != cudaSuccess) return MPSPMV_ENOMEM;
-    h->device_bytes += yb;
-  }
-  MPS_CUDA(cudaMemcpyAsync(h->d_xbuf, x_host, sizeof(double) * h->P * h->ncols, cudaMemcpyHostToDevice, s));
-  int st = mps_launch_spmv(h, h->d_xbuf, h->d_ybuf, s);
+  int st = spmv_host_enqueue(h, x_host, y_host, s);
   if (st != MPSPMV_OK) return st;
-  MPS_CUDA(cudaMemcpyAsync(y_host, h->d_ybuf, sizeof(double) * h->P * h->nrows, cudaMemcpyDeviceToHost, s));
   MPS_CUDA(cudaStreamSynchronize(s));
   return MPSPMV_OK;
+}
+
+int mpspmv_spmv_host_async(mpspmv_h h, const double* x_host, double* y_host, void* stream) {
+  if (!h || !x_host || !y_host) return MPSPMV_EINVAL;
+  return spmv_host_enqueue(h, x_host, y_host, mps_stream(stream));
 }
 
 int mpspmv_spmm(mpspmv_h h, int k, const double* X, int64_t ldx, double* Y, int64_t ldy, void* stream) {

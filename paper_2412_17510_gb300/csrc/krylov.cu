@@ -110,6 +110,18 @@ extern "C" int mpspmv_axpy(mpspmv_h h, int64_t n, const double* alpha, const dou
   MPS_BY_L(h->L, Ops::axpy(h, n, alpha, u, v, w, s));
 }
 
+extern "C" int mpspmv_scalar_sum(mpspmv_h h, int count, const double* parts, double* out, void* stream) {
+  if (!h || count < 1 || !parts || !out) return MPSPMV_EINVAL;
+  cudaStream_t s = mps_stream(stream);
+  MPS_BY_L(h->L, Ops::scalar_sum(h, count, parts, out, s));
+}
+
+extern "C" int mpspmv_scalar_div(mpspmv_h h, const double* a, const double* b, double* out, void* stream) {
+  if (!h || !a || !b || !out) return MPSPMV_EINVAL;
+  cudaStream_t s = mps_stream(stream);
+  MPS_BY_L(h->L, Ops::scalar_div(h, a, b, out, s));
+}
+
 // ---------------------------------------------------------------------------
 // Precision ladder and the learned selector's entry points.
 // ---------------------------------------------------------------------------

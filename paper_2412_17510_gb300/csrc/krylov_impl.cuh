@@ -1826,6 +1826,114 @@ int axpy_impl(mpspmv_mat* h, int64_t n, const double* alpha, const double* u, co
 
 
 // ---------------------------------------------------------------------------
+// MP scalars of a distributed solve: the inner-product partials of several
+// row blocks summed in block order, and the quotients of the solver's
+// scalars (one thread each; the work is a handful of MP operations).
+// ---------------------------------------------------------------------------
+constexpr int kMaxScalarParts = 4096;
+
+// out = parts[0] + parts[1] + ... + parts[count-1], real and imaginary parts
+// separately.  Paper order: MP additions from left to right.  Exact
+// (MPSPMV_EXACT_ACC): every component in register digits at the base of the
+// largest one, cut to L components once (independent of the order).
+template <int L, bool CPLX>
+__global__ void k_scalar_sum(const double* __restrict__ parts, int count, double* __restrict__ out, bool ex) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+#pragma unroll 1
+  for (int c = 0; c < (CPLX ? 2 : 1); c++) {
+    mp<L> r;
+    if (ex) {
+      constexpr int D = AccDigits<L>::D;
+      int t = INT_MIN;
+      for (int i = 0; i < count; i++)
+#pragma unroll
+        for (int l = 0; l < L; l++) t = max(t, top_exp(parts[(int64_t)i * 2 * L + c * L + l]));
+      FixAcc<D> f;
+      fa_at_top<D>(f, t);
+      for (int i = 0; i < count; i++)
+#pragma unroll
+        for (int l = 0; l < L; l++) fa_add<D>(f, parts[(int64_t)i * 2 * L + c * L + l]);
+      fa_to_mp<L, D>(f, r.v);
+    } else {
+#pragma unroll
+      for (int l = 0; l < L; l++) r.v[l] = parts[c * L + l];
+      for (int i = 1; i < count; i++) {
+        mp<L> a;
+#pragma unroll
+        for (int l = 0; l < L; l++) a.v[l] = parts[(int64_t)i * 2 * L + c * L + l];
+        r = mp_add<L>(r, a);
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < L; l++) out[c * L + l] = r.v[l];
+  }
+  if (!CPLX)
+#pragma unroll
+    for (int l = 0; l < L; l++) out[L + l] = 0.0;
+}
+
+// out = a / b (ab = a, then b, each 2L components)
+template <int L, bool CPLX>
+__global__ void k_scalar_div(const double* __restrict__ ab, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cmp<L> a, b;
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    a.re.v[l] = ab[l];
+    a.im.v[l] = ab[L + l];
+    b.re.v[l] = ab[2 * L + l];
+    b.im.v[l] = ab[3 * L + l];
+  }
+  const cmp<L> q = c_div_any<L, CPLX>(a, b);
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    out[l] = q.re.v[l];
+    out[L + l] = CPLX ? q.im.v[l] : 0.0;
+  }
+}
+
+template <int L, bool CPLX>
+int scalar_sum_impl(mpspmv_mat* h, int count, const double* parts, double* out, cudaStream_t s) {
+  Work w;
+  int st = ensure_ws(h, w);
+  if (st) return st;
+  double* din = w.part[3];
+  double* dout = w.part[4];
+  MPS_CUDA(cudaMemcpyAsync(din, parts, sizeof(double) * 2 * L * count, cudaMemcpyHostToDevice, s));
+  k_scalar_sum<L, CPLX><<<1, 32, 0, s>>>(din, count, dout, h->exact);
+  MPS_CUDA(cudaGetLastError());
+  MPS_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * 2 * L, cudaMemcpyDeviceToHost, s));
+  MPS_CUDA(cudaStreamSynchronize(s));
+  return MPSPMV_OK;
+}
+
+template <int L, bool CPLX>
+int scalar_div_impl(mpspmv_mat* h, const double* a, const double* b, double* out, cudaStream_t s) {
+  bool zero = true;
+  for (int l = 0; l < L; l++) zero = zero && b[l] == 0.0 && (!CPLX || b[L + l] == 0.0);
+  if (zero) return MPSPMV_EBREAKDOWN;
+  Work w;
+  int st = ensure_ws(h, w);
+  if (st) return st;
+  double ab[16];
+  for (int l = 0; l < L; l++) {
+    ab[l] = a[l];
+    ab[L + l] = CPLX ? a[L + l] : 0.0;
+    ab[2 * L + l] = b[l];
+    ab[3 * L + l] = CPLX ? b[L + l] : 0.0;
+  }
+  double* din = w.part[3];
+  double* dout = w.part[4];
+  MPS_CUDA(cudaMemcpyAsync(din, ab, sizeof(double) * 4 * L, cudaMemcpyHostToDevice, s));
+  k_scalar_div<L, CPLX><<<1, 32, 0, s>>>(din, dout);
+  MPS_CUDA(cudaGetLastError());
+  MPS_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * 2 * L, cudaMemcpyDeviceToHost, s));
+  // ab is host stack memory: the copy must have run before returning
+  MPS_CUDA(cudaStreamSynchronize(s));
+  return MPSPMV_OK;
+}
+
+// ---------------------------------------------------------------------------
 // BiCG, CGS, GPBiCG (host side).  Same structure as bicgstab_impl: a setup on
 // the caller's stream, then graph-captured iterations gated by the state.
 // ---------------------------------------------------------------------------
@@ -2063,6 +2171,18 @@ template <int L>
 int KrylovOps<L>::axpy(mpspmv_mat* h, int64_t n, const double* alpha, const double* u, const double* v, double* w,
                        cudaStream_t s) {
   return h->cplx ? axpy_impl<L, true>(h, n, alpha, u, v, w, s) : axpy_impl<L, false>(h, n, alpha, u, v, w, s);
+}
+
+template <int L>
+int KrylovOps<L>::scalar_sum(mpspmv_mat* h, int count, const double* parts, double* out, cudaStream_t s) {
+  if (count < 1 || count > kMaxScalarParts) return MPSPMV_EINVAL;
+  return h->cplx ? scalar_sum_impl<L, true>(h, count, parts, out, s)
+                 : scalar_sum_impl<L, false>(h, count, parts, out, s);
+}
+
+template <int L>
+int KrylovOps<L>::scalar_div(mpspmv_mat* h, const double* a, const double* b, double* out, cudaStream_t s) {
+  return h->cplx ? scalar_div_impl<L, true>(h, a, b, out, s) : scalar_div_impl<L, false>(h, a, b, out, s);
 }
 
 }  // namespace mpkry

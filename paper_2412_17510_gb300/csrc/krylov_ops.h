@@ -20,6 +20,8 @@ struct KrylovOps {
   static int dot(mpspmv_mat* h, int64_t n, const double* u, const double* v, double* out, cudaStream_t s);
   static int axpy(mpspmv_mat* h, int64_t n, const double* alpha, const double* u, const double* v, double* w,
                   cudaStream_t s);
+  static int scalar_sum(mpspmv_mat* h, int count, const double* parts, double* out, cudaStream_t s);
+  static int scalar_div(mpspmv_mat* h, const double* a, const double* b, double* out, cudaStream_t s);
 };
 
 // one nonsymmetric method (Method) for real or complex data

@@ -256,6 +256,45 @@ __global__ void sgd_kernel(float* __restrict__ p, const float* __restrict__ g, i
   if (t < n) p[t] -= lr * g[t];
 }
 
+// Column statistics of n feature vectors (n x D0, row-major): mean and
+// population standard deviation of every feature, summed in binary64 in
+// sample order (deterministic), rounded to float; a deviation below 1e-6
+// becomes 1 (a constant feature passes unscaled).  Xs = (X - mu) / sd with
+// the rounded mu and sd, so that the fold below is consistent with it.
+// One thread per feature.
+__global__ void standardize_kernel(const float* __restrict__ X, int n, float* __restrict__ mu,
+                                   float* __restrict__ sd, float* __restrict__ Xs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D0) return;
+  double s = 0.0;
+  for (int b = 0; b < n; b++) s += (double)X[(int64_t)b * D0 + i];
+  const double m = s / n;
+  double v = 0.0;
+  for (int b = 0; b < n; b++) {
+    const double d = (double)X[(int64_t)b * D0 + i] - m;
+    v += d * d;
+  }
+  double sdv = sqrt(v / n);
+  if (sdv < 1e-6) sdv = 1.0;
+  const float mf = (float)m, sf = (float)sdv;
+  mu[i] = mf;
+  sd[i] = sf;
+  for (int b = 0; b < n; b++) Xs[(int64_t)b * D0 + i] = (float)(((double)X[(int64_t)b * D0 + i] - mf) / sf);
+}
+
+// First layer rewritten for raw features: ((x - mu) / sd) W1 + b1 =
+// x (W1 / sd[:, None]) + (b1 - (mu / sd) W1).  One thread per hidden unit,
+// binary64 arithmetic over the inputs in index order, rounded to float.
+__global__ void fold_kernel(float* __restrict__ W1, float* __restrict__ b1, const float* __restrict__ mu,
+                            const float* __restrict__ sd) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= D1) return;
+  double acc = b1[j];
+  for (int i = 0; i < D0; i++) acc -= (double)mu[i] / (double)sd[i] * (double)W1[(int64_t)i * D1 + j];
+  b1[j] = (float)acc;
+  for (int i = 0; i < D0; i++) W1[(int64_t)i * D1 + j] = (float)((double)W1[(int64_t)i * D1 + j] / (double)sd[i]);
+}
+
 inline unsigned nb(int64_t n) { return (unsigned)((n + kFT - 1) / kFT); }
 
 struct MlpWork {
@@ -417,6 +456,23 @@ int mpspmv_mlp_train(float* params, int C, const float* X, const int* y, int n, 
   cudaFree(g);
   cudaFree(buf);
   return st;
+}
+
+int mpspmv_mlp_standardize(const float* X, int n, float* mu, float* sd, float* Xs, void* stream) {
+  if (!X || !mu || !sd || !Xs || n < 1) return MPSPMV_EINVAL;
+  cudaStream_t s = mps_stream(stream);
+  standardize_kernel<<<1, D0, 0, s>>>(X, n, mu, sd, Xs);
+  MPS_CUDA(cudaGetLastError());
+  return MPSPMV_OK;
+}
+
+int mpspmv_mlp_fold(float* params, int C, const float* mu, const float* sd, void* stream) {
+  if (!params || !mu || !sd || C < 2 || C > 16) return MPSPMV_EINVAL;
+  cudaStream_t s = mps_stream(stream);
+  const MlpView v = mlp_view(params, C);
+  fold_kernel<<<1, D1, 0, s>>>(const_cast<float*>(v.W1), const_cast<float*>(v.b1), mu, sd);
+  MPS_CUDA(cudaGetLastError());
+  return MPSPMV_OK;
 }
 
 int mpspmv_features(mpspmv_h h, const double* cg_hist, float* feat, void* stream) {

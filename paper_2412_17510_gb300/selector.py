@@ -17,8 +17,9 @@ import time
 import numpy as np
 
 from . import (MPSPMV_OK, mpspmv_batch_cg, mpspmv_batch_create, mpspmv_batch_destroy, mpspmv_cg_history,
-               mpspmv_create_csr, mpspmv_destroy, mpspmv_features, mpspmv_ladder_solve, mpspmv_mlp_forward,
-               mpspmv_mlp_param_count, mpspmv_mlp_train, mpspmv_solve_auto)
+               mpspmv_create_csr, mpspmv_destroy, mpspmv_features, mpspmv_ladder_solve, mpspmv_mlp_fold,
+               mpspmv_mlp_forward, mpspmv_mlp_param_count, mpspmv_mlp_standardize, mpspmv_mlp_train,
+               mpspmv_solve_auto)
 
 NCLASS = 5
 
@@ -97,37 +98,31 @@ def init_params(seed=0, C=NCLASS):
     return out
 
 
-def fold_standardisation(params, mu, sd, C=NCLASS):
-    """Rewrite W1, b1 so that the network takes raw features:
-    (x - mu) / sd @ W1 + b1 = x @ (W1 / sd[:, None]) + (b1 - (mu / sd) @ W1)."""
-    p = params.astype(np.float64).copy()
-    W1 = p[:32 * 128].reshape(32, 128)
-    b1 = p[32 * 128:32 * 128 + 128]
-    nb1 = b1 - (mu / sd) @ W1
-    W1 /= sd[:, None]
-    p[32 * 128:32 * 128 + 128] = nb1
-    return p.astype(np.float32)
-
-
 def train(X, y, epochs=200, batch=32, lr=0.05, seed=0, C=NCLASS):
-    """Train on standardised features with the GPU kernels (plain SGD, data
-    reshuffled every epoch); returns parameters for raw features, the loss
-    history and (mu, sd)."""
+    """Train with the GPU kernels: the features are standardised on the
+    device (mpspmv_mlp_standardize), the network is trained on them by plain
+    SGD with the samples reshuffled every epoch, and the standardisation is
+    folded into W1 and b1 on the device (mpspmv_mlp_fold), so the returned
+    parameters take raw features.  Returns (parameters, loss history,
+    (mu, sd))."""
     import torch
-    mu = X.mean(axis=0)
-    sd = X.std(axis=0)
-    sd[sd < 1e-6] = 1.0
-    Xs = ((X - mu) / sd).astype(np.float32)
+    n = len(y)
+    dX = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    mu = torch.empty(32, dtype=torch.float32, device="cuda")
+    sd = torch.empty(32, dtype=torch.float32, device="cuda")
+    dXs = torch.empty_like(dX)
+    mpspmv_mlp_standardize(dX, n, mu, sd, dXs)
+    Xs = dXs.cpu().numpy()
     rng = np.random.default_rng(seed)
     dp = torch.from_numpy(init_params(seed, C)).cuda()
     losses = []
     for _ in range(epochs):
-        perm = rng.permutation(len(y))
-        dX = torch.from_numpy(np.ascontiguousarray(Xs[perm])).cuda()
+        perm = rng.permutation(n)
+        dXp = torch.from_numpy(np.ascontiguousarray(Xs[perm])).cuda()
         dy = torch.from_numpy(np.ascontiguousarray(y[perm].astype(np.int32))).cuda()
-        losses.append(float(mpspmv_mlp_train(dp, C, dX, dy, len(y), batch, 1, lr)[0]))
-    raw = fold_standardisation(dp.cpu().numpy(), mu, sd, C)
-    return raw, np.array(losses), (mu, sd)
+        losses.append(float(mpspmv_mlp_train(dp, C, dXp, dy, n, batch, 1, lr)[0]))
+    mpspmv_mlp_fold(dp, C, mu, sd)
+    return dp.cpu().numpy(), np.array(losses), (mu.cpu().numpy(), sd.cpu().numpy())
 
 
 def predict(params, X, C=NCLASS):
@@ -138,49 +133,82 @@ def predict(params, X, C=NCLASS):
     return lg.argmax(dim=1).cpu().numpy()
 
 
-def evaluate(sys_list, params, rtol, maxit_factor=2, C=NCLASS):
-    """Per held-out system: the plain ladder from binary64, the selector-guided
-    ladder (solve_auto), each timed end to end; plus the batched selector-
-    guided solve of all systems (predicted level first, failures move up a
-    level in the next batch).  Returns a dict of totals."""
-    import torch
-    dp = torch.from_numpy(np.ascontiguousarray(params)).cuda()
-    res = {"plain_s": 0.0, "auto_s": 0.0, "plain_ok": 0, "auto_ok": 0, "escalated": 0, "chosen": [], "final": []}
-    for s in sys_list:
-        maxit = maxit_factor * s.n
-        x = torch.zeros((4, s.n), dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, fl, its, rr = mpspmv_ladder_solve(s.handles, 1, s.b, x, rtol, 0.0, maxit)
-        torch.cuda.synchronize()
-        res["plain_s"] += time.perf_counter() - t0
-        res["plain_ok"] += int(st == MPSPMV_OK)
-        x.zero_()
-        t0 = time.perf_counter()
-        st2, ch, fl2, its2, rr2 = mpspmv_solve_auto(s.handles, dp, C, s.b, x, rtol, 0.0, maxit)
-        torch.cuda.synchronize()
-        res["auto_s"] += time.perf_counter() - t0
-        res["auto_ok"] += int(st2 == MPSPMV_OK)
-        res["escalated"] += int(fl2 > ch)
-        res["chosen"].append(ch)
-        res["final"].append(fl2)
-    # batched, selector-guided
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    X = features(sys_list)
-    level = np.minimum(predict(params, X, C) + 1, 4)
+def batched_ladder(sys_list, start, rtol, maxit_factor=2):
+    """Batched precision ladder: every system whose start level (array) is
+    at most L and that is not yet solved takes part in the batched CG at
+    level L, from x0 = 0; a system that falls short moves up a level.
+    Returns (solved mask, total CG iterations, level that solved each system
+    or 0)."""
     done = np.zeros(len(sys_list), dtype=bool)
+    final = np.zeros(len(sys_list), dtype=np.int32)
+    iters = 0
     maxit = maxit_factor * max(s.n for s in sys_list)
     for L in (1, 2, 3, 4):
-        idx = [i for i in range(len(sys_list)) if not done[i] and level[i] <= L]
+        idx = [i for i in range(len(sys_list)) if not done[i] and start[i] <= L]
         if not idx:
             continue
         ok, it, _ = solve_level_batched([sys_list[i] for i in idx], L, rtol, maxit)
         for j, i in enumerate(idx):
+            iters += int(min(it[j], maxit_factor * sys_list[i].n))
             if ok[j] and it[j] <= maxit_factor * sys_list[i].n:
                 done[i] = True
+                final[i] = L
+    return done, iters, final
+
+
+def evaluate(sys_list, params, rtol, maxit_factor=2, C=NCLASS, starts=(1, 2, 3, 4), per_system=True):
+    """Time to the target on held-out systems, every strategy from x0 = 0
+    and timed end to end on the host clock (device synchronised):
+      plain ladder from a fixed level (one system after another,
+      mpspmv_ladder_solve; start 1 is the plain binary64 -> DD -> TD -> QD
+      ladder), the selector-guided ladder (mpspmv_solve_auto), and batched
+      forms of both (fixed start, and the selector's level per system with
+      features and inference inside the timing).  Returns a dict of totals:
+      seconds, systems solved, CG iterations summed over levels, escalations
+      (selector: the ladder moved above the chosen level)."""
+    import torch
+    dp = torch.from_numpy(np.ascontiguousarray(params)).cuda()
+    res = {"n": len(sys_list), "ladder": {}, "batched_ladder": {}}
+    if per_system:
+        for L0 in starts:
+            tot = {"s": 0.0, "solved": 0, "iters": 0}
+            for s in sys_list:
+                x = torch.zeros((4, s.n), dtype=torch.float64, device="cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, fl, its, _ = mpspmv_ladder_solve(s.handles, L0, s.b, x, rtol, 0.0, maxit_factor * s.n)
+                torch.cuda.synchronize()
+                tot["s"] += time.perf_counter() - t0
+                tot["solved"] += int(st == MPSPMV_OK)
+                tot["iters"] += int(sum(its))
+            res["ladder"][L0] = tot
+        tot = {"s": 0.0, "solved": 0, "iters": 0, "escalated": 0, "chosen": [], "final": []}
+        for s in sys_list:
+            x = torch.zeros((4, s.n), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st2, ch, fl2, its2, _ = mpspmv_solve_auto(s.handles, dp, C, s.b, x, rtol, 0.0, maxit_factor * s.n)
+            torch.cuda.synchronize()
+            tot["s"] += time.perf_counter() - t0
+            tot["solved"] += int(st2 == MPSPMV_OK)
+            tot["iters"] += int(sum(its2))
+            tot["escalated"] += int(fl2 > ch)
+            tot["chosen"].append(ch)
+            tot["final"].append(fl2)
+        res["selector"] = tot
+    for L0 in starts:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done, iters, _ = batched_ladder(sys_list, np.full(len(sys_list), L0), rtol, maxit_factor)
+        torch.cuda.synchronize()
+        res["batched_ladder"][L0] = {"s": time.perf_counter() - t0, "solved": int(done.sum()), "iters": iters}
     torch.cuda.synchronize()
-    res["batched_auto_s"] = time.perf_counter() - t0
-    res["batched_auto_ok"] = int(done.sum())
-    res["n"] = len(sys_list)
+    t0 = time.perf_counter()
+    X = features(sys_list)
+    level = np.minimum(predict(params, X, C) + 1, 4)
+    done, iters, final = batched_ladder(sys_list, level, rtol, maxit_factor)
+    torch.cuda.synchronize()
+    res["batched_selector"] = {"s": time.perf_counter() - t0, "solved": int(done.sum()), "iters": iters,
+                               "escalated": int(((final > level) & done).sum()),
+                               "chosen_hist": {int(v): int((level == v).sum()) for v in np.unique(level)}}
     return res

@@ -168,22 +168,28 @@ def test_select_precision_maps_classes_and_solve_auto():
 
 
 def test_trained_selector_saves_ladder_iterations():
-    """What the learned part gains over the method without it: the network is
-    trained by the float32 kernels on labels from the method's own batched
-    CG solves (graded SPD systems A = D (L L^T + I) D, n in [40, 80], cond
-    10^U[8, 24], target relative residual 1e-30, cap 30 n per level), then
-    ten held-out systems are solved twice.  The plain ladder starts at
-    binary64, whose CG meets the recurrence test long before its true
-    residual could reach 1e-30, and climbs level by level; the selector-
-    guided ladder starts at the predicted level.  It needs far fewer CG
-    iterations in total and solves as many systems (within two: a plain
-    ladder's warm starts from lower levels can rescue a system that a cold
-    start at the chosen level leaves at the cap)."""
+    """What the learned part gains over the method without it, and over a
+    constant rule: the network is trained by the float32 kernels on labels
+    from the method's own batched CG solves (graded SPD systems
+    A = D (L L^T + I) D, n in [40, 80], cond 10^U[8, 24], target relative
+    residual 1e-30, cap 30 n per level), then 16 held-out systems are solved
+    by the plain ladder from every fixed start level (binary64, DD, TD, QD)
+    and by the selector-guided ladder.  Binary64 can never reach 1e-30, so
+    the plain ladder from binary64 spends its cap there; a constant start at
+    DD or TD spends its cap on every system that needs a higher level.  The
+    selector-guided ladder needs fewer than 0.8 of the CG iterations of the
+    best of the binary64, DD and TD starts and solves at least as many
+    systems as each of them, with at most one fewer than the best start (a
+    ladder's warm start from a lower level can rescue a system that a cold
+    start leaves at the cap).  The QD start is reported beside them: it needs
+    the fewest iterations of all (QD's iteration counts are the lowest), and
+    the selector's gain over it is time, not iterations, where TD is cheaper
+    per iteration than QD."""
     from paper_2412_17510_gb300 import selector as sel
     rng = np.random.default_rng(5)
     systems = []
     try:
-        for i in range(50):
+        for i in range(56):
             n = int(rng.integers(40, 81))
             coo, b = workloads.selector_system(n, float(rng.uniform(8, 24)), seed=2000 + i)
             systems.append(sel.System(coo, b))
@@ -193,23 +199,54 @@ def test_trained_selector_saves_ladder_iterations():
         assert not (y == 0).any()  # binary64 never reaches 1e-30
         params, losses, _ = sel.train(X, y, epochs=200, batch=32, lr=0.05)
         assert losses[-1] < losses[0]
-        dp = to_dev(params)
-        plain_its = auto_its = plain_ok = auto_ok = 0
-        for s in held_out:
-            maxit = 30 * s.n
-            x = torch.zeros((4, s.n), dtype=torch.float64, device="cuda")
-            st, fl, its, rr = mps.mpspmv_ladder_solve(s.handles, 1, s.b, x, 1e-30, 0.0, maxit)
-            plain_its += sum(its)
-            plain_ok += int(st == mps.MPSPMV_OK)
-            x.zero_()
-            st2, ch, fl2, its2, rr2 = mps.mpspmv_solve_auto(s.handles, dp, sel.NCLASS, s.b, x, 1e-30, 0.0, maxit)
-            auto_its += sum(its2)
-            auto_ok += int(st2 == mps.MPSPMV_OK)
-            assert fl2 >= ch >= 1
-        print("held-out CG iterations: plain ladder %d, selector-guided %d; solved %d / %d of %d"
-              % (plain_its, auto_its, plain_ok, auto_ok, len(held_out)))
-        assert auto_its < 0.8 * plain_its
-        assert auto_ok >= plain_ok - 2
+        ev = sel.evaluate(held_out, params, 1e-30, maxit_factor=30)
+        lad, auto = ev["ladder"], ev["selector"]
+        print("held-out CG iterations / solved: " + ", ".join(
+            "start %d: %d / %d" % (L0, lad[L0]["iters"], lad[L0]["solved"]) for L0 in (1, 2, 3, 4)) +
+            "; selector: %d / %d (escalated %d) of %d" % (auto["iters"], auto["solved"], auto["escalated"],
+                                                          len(held_out)))
+        for c, f in zip(auto["chosen"], auto["final"]):
+            assert f >= c >= 1
+        best = min(lad[L0]["iters"] for L0 in (1, 2, 3))
+        assert auto["iters"] < 0.8 * best
+        assert auto["solved"] >= max(lad[L0]["solved"] for L0 in (1, 2, 3)) - 1
+        assert auto["solved"] >= lad[1]["solved"]
     finally:
         for s in systems:
             s.free()
+
+
+def test_standardisation_kernels_match_numpy():
+    """mpspmv_mlp_standardize against a float64 numpy computation, and the
+    fold into W1, b1: the folded network on raw features gives the logits of
+    the unfolded network on standardised features (float tolerance)."""
+    C = 5
+    rng = np.random.default_rng(9)
+    n = 300
+    X = (rng.standard_normal((n, 32)) * 10.0 ** rng.uniform(-3, 3, 32) + rng.uniform(-50, 50, 32)).astype(np.float32)
+    X[:, 7] = 3.25  # a constant feature keeps sd = 1
+    dX = to_dev(X)
+    mu = torch.empty(32, dtype=torch.float32, device="cuda")
+    sd = torch.empty(32, dtype=torch.float32, device="cuda")
+    Xs = torch.empty_like(dX)
+    mps.mpspmv_mlp_standardize(dX, n, mu, sd, Xs)
+    torch.cuda.synchronize()
+    X64 = X.astype(np.float64)
+    mu_ref = X64.mean(axis=0)
+    sd_ref = X64.std(axis=0)
+    sd_ref[sd_ref < 1e-6] = 1.0
+    np.testing.assert_allclose(mu.cpu().numpy(), mu_ref, rtol=1e-6, atol=1e-6 * np.abs(X64).max())
+    np.testing.assert_allclose(sd.cpu().numpy(), sd_ref, rtol=1e-6)
+    assert sd.cpu().numpy()[7] == 1.0
+    xs_ref = (X64 - mu.cpu().numpy().astype(np.float64)) / sd.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(Xs.cpu().numpy(), xs_ref, rtol=1e-6, atol=1e-6)
+    params = [p.astype(np.float32) for p in omlp.init(C, seed=4)]
+    dp = to_dev(flat_params(params))
+    lg_std = torch.empty((n, C), dtype=torch.float32, device="cuda")
+    mps.mpspmv_mlp_forward(dp, C, Xs, n, lg_std)
+    mps.mpspmv_mlp_fold(dp, C, mu, sd)
+    lg_raw = torch.empty((n, C), dtype=torch.float32, device="cuda")
+    mps.mpspmv_mlp_forward(dp, C, dX, n, lg_raw)
+    torch.cuda.synchronize()
+    a, b = lg_raw.cpu().numpy(), lg_std.cpu().numpy()
+    np.testing.assert_allclose(a, b, rtol=1e-3, atol=1e-3 * np.abs(b).max())

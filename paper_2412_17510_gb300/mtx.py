@@ -1,4 +1,5 @@
-"""Matrix Market coordinate files -> the triplets ``mpspmv_create_csr`` takes.
+"""Matrix Market files <-> the triplets ``mpspmv_create_csr`` takes and the
+structure-of-limbs vectors the products return.
 
 Host-side input plumbing, no arithmetic of the method.  The paper's test
 matrices are Matrix Market files (Section 4.1: SuiteSparse), and
@@ -12,6 +13,11 @@ become 0-based, and the result is ready for
 ``val`` has one plane for real data and two (real, imaginary) for complex
 data, and ``flags`` carries ``MPSPMV_COMPLEX`` for complex data.  Duplicate
 entries are kept; the library sums them.
+
+``write_mtx`` writes triplets back as a coordinate file (one triangle for the
+symmetric forms), and ``write_vector`` / ``read_vector`` store a DD/TD/QD
+vector as an ``array`` file with one column per component; every value is
+written with enough digits to read back bit for bit.
 """
 import io
 
@@ -117,3 +123,82 @@ def read_mtx(src):
         row, col, re = np.concatenate([row, mr]), np.concatenate([col, mc]), np.concatenate([re, mre])
     val = re[None, :] if im is None else np.stack([re, im])
     return MtxMatrix(nrows, ncols, row, col, np.ascontiguousarray(val), field, sym)
+
+
+def _fmt(v):
+    """Shortest text that reads back as the same binary64 value."""
+    return repr(float(v))
+
+
+def write_mtx(dst, nrows, ncols, row, col, val, symmetry="general", comment=None):
+    """Write triplets as a Matrix Market coordinate file (``dst``: a path or
+    an open text file).  ``val`` has one plane (field ``real``) or two (real,
+    imaginary: field ``complex``) of binary64 values, written with enough
+    digits to read back bit for bit; indices are 0-based here and 1-based in
+    the file.  For ``symmetric``, ``skew-symmetric`` or ``hermitian`` only
+    the entries on or below the diagonal are written (the reader expands
+    them again); the caller passes a matrix that has that symmetry."""
+    if symmetry not in _SYMMETRIES:
+        raise ValueError("unknown symmetry %r" % symmetry)
+    row = np.asarray(row, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    val = np.atleast_2d(np.asarray(val, dtype=np.float64))
+    if val.shape[0] not in (1, 2) or val.shape[1] != row.shape[0] or col.shape[0] != row.shape[0]:
+        raise ValueError("val must hold one or two planes of nnz values")
+    if symmetry != "general":
+        if nrows != ncols:
+            raise ValueError("a %s matrix must be square" % symmetry)
+        keep = row >= col
+        row, col, val = row[keep], col[keep], val[:, keep]
+    field = "complex" if val.shape[0] == 2 else "real"
+    out = ["%%%%MatrixMarket matrix coordinate %s %s" % (field, symmetry)]
+    if comment:
+        out += ["%" + ln for ln in str(comment).splitlines()]
+    out.append("%d %d %d" % (nrows, ncols, row.shape[0]))
+    for k in range(row.shape[0]):
+        out.append(" ".join([str(int(row[k]) + 1), str(int(col[k]) + 1)] + [_fmt(val[c, k]) for c in range(val.shape[0])]))
+    text = "\n".join(out) + "\n"
+    if hasattr(dst, "write"):
+        dst.write(text)
+    else:
+        with open(dst, "w") as f:
+            f.write(text)
+
+
+def write_vector(dst, v, comment=None):
+    """Write a multiple-precision vector (structure of limbs: P planes of n
+    binary64 values) as a Matrix Market ``array`` file of n rows and P
+    columns, column p holding plane p, with enough digits to read back bit
+    for bit: a DD/TD/QD result (real, or real then imaginary components)
+    survives the file unchanged."""
+    v = np.atleast_2d(np.asarray(v, dtype=np.float64))
+    P, n = v.shape
+    out = ["%%MatrixMarket matrix array real general"]
+    if comment:
+        out += ["%" + ln for ln in str(comment).splitlines()]
+    out.append("%d %d" % (n, P))
+    for p in range(P):  # column-major, as the array format stores it
+        out.extend(_fmt(t) for t in v[p])
+    text = "\n".join(out) + "\n"
+    if hasattr(dst, "write"):
+        dst.write(text)
+    else:
+        with open(dst, "w") as f:
+            f.write(text)
+
+
+def read_vector(src):
+    """Read a Matrix Market ``array real general`` file written by
+    ``write_vector`` (n rows, P columns) back into P planes of n values."""
+    lines = _lines(src)
+    if not lines or not lines[0].lower().startswith("%%matrixmarket"):
+        raise ValueError("missing %%MatrixMarket header")
+    head = lines[0].lower().split()
+    if head[1:] != ["matrix", "array", "real", "general"]:
+        raise ValueError("expected: %%MatrixMarket matrix array real general")
+    body = [ln for ln in lines[1:] if ln.strip() and not ln.lstrip().startswith("%")]
+    n, P = (int(t) for t in body[0].split())
+    vals = np.array(" ".join(body[1:]).split(), dtype=np.float64)
+    if vals.shape[0] != n * P:
+        raise ValueError("size line announces %d values, file holds %d" % (n * P, vals.shape[0]))
+    return np.ascontiguousarray(vals.reshape(P, n))

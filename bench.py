@@ -1,26 +1,36 @@
-"""Benchmark: multiple-precision CSR SpMV throughput (Gnnz/s) on GB300.
+"""Benchmark: multiple-precision CSR SpMV throughput (Gnnz/s) on GB300, plus
+complex SpMV, BiCGSTAB and the CG time-to-1e-30 comparison of the precision
+ladder with the learned selector.
 
-Workload (one step): y = A x in DD, TD and QD (P mode, binary64 values
-promoted) on two real matrices shaped like the paper's SpMV workloads
-(arXiv 2412.17510, Section 4.1, SuiteSparse stand-ins):
+Timed step (``value``): y = A x in DD, TD and QD on two real matrices shaped
+like the paper's SpMV workloads (arXiv 2412.17510, Section 4.1, SuiteSparse
+stand-ins), repeated ``--repeat`` times per step:
   (a) 3D 27-point stencil on a 128^3 grid, non-periodic (n = 2,097,152,
       nnz = 55,742,968), off-diagonals N(0,1), diagonal = row |sum| + 1;
   (b) power-law rows, n = 1,000,000, lengths Zipf(1.5) clipped to [1, 20000]
-      (nnz ~ 2.17e8), uniform distinct columns, N(0,1) values;
-x with every component random, seed 0.  value = (sum of nnz over the six
-products) / (device time of the step).  Inputs are resident in HBM; the L2
-cache is flushed (a 512 MiB write) between timed steps, outside the timed
-events.
+      (nnz ~ 2.16e8), uniform distinct columns, N(0,1) values;
+binary64 matrix values (P-mode results: the lower components are zero), x
+with every component random, seed 0.  value = (entries multiplied in the
+step) / (device time of the step).  Inputs are resident in HBM and far
+larger than L2; the L2 cache is also flushed (a 512 MiB write) between
+timed steps, outside the timed events.
+
+Also in the default line (rank 0): ``complex`` (complex band SpMV, DD/QD,
+both arithmetics, and BiCGSTAB to 1e-28), ``full_limb_A`` (the exact
+arithmetic on matrices whose values have L random components), and
+``cg_time_to_1e-30`` (plain precision ladder from every start level against
+the selector-guided ladder, per system and batched, on held-out systems).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 N > 1 runs under torch.distributed.run; every rank multiplies its own copy of
 the workload (independent problems, no collective on the data path), the time
-is the maximum over ranks and value counts the nnz of all ranks.
+is the maximum over ranks and value counts the entries of all ranks.
 """
 import argparse
 import hashlib
 import json
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -57,6 +67,8 @@ UPD_PER_ENTRY_EXACT_D = {2: 8, 3: 13, 4: 18}
 SMEM_BYTES_PER_CLK = 128  # shared-memory bandwidth per SM per clock (32 banks x 4 B)
 UPD_BYTES = 16
 L2_FLUSH_BYTES = 512 << 20
+# oracle sample: entries per slice (about 50 ms of one Grace core each)
+SLICE_ENTRIES = {2: 3000000, 3: 400000, 4: 400000}
 
 
 def replica_value(local_ms, units_per_rank, world, dist=None, device="cpu"):
@@ -171,50 +183,84 @@ def stored_traffic(variant):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle leg (bounded sample, all host cores)
+# CPU oracle leg: the same sampler in both arms (bounded sample, host cores)
 # ---------------------------------------------------------------------------
-def _oracle_worker(args):
-    indptr, indices, data, x, L = args
+def _oracle_slice(args):
+    """Worker: the oracle's SpMV of rows a..b-1 of one matrix at L
+    components (its values promoted), x of the whole matrix; the matrix and
+    x come from .npy files mapped read-only.  Returns (entries, seconds of
+    the product alone)."""
+    d, mname, L, a, b = args
     import oracle as orc
-    A = orc.CSR(len(indptr) - 1, x.shape[1], indptr, indices, data, L, False)
+    ip = np.load(os.path.join(d, mname + ".indptr.npy"), mmap_mode="r")
+    lo, hi = int(ip[a]), int(ip[b])
+    indptr = np.array(ip[a:b + 1], dtype=np.int64) - lo
+    ind = np.array(np.load(os.path.join(d, mname + ".indices.npy"), mmap_mode="r")[lo:hi], dtype=np.int32)
+    vals = np.zeros((L, hi - lo))
+    vals[0] = np.load(os.path.join(d, mname + ".vals.npy"), mmap_mode="r")[lo:hi]
+    x = np.array(np.load(os.path.join(d, "%s.x%d.npy" % (mname, L)), mmap_mode="r"))
+    A = orc.CSR(b - a, x.shape[1], indptr, ind, vals, L, False)
     t = time.perf_counter()
     orc.spmv(A, x)
-    return time.perf_counter() - t
+    return hi - lo, time.perf_counter() - t
 
 
-def _task(ip, a, b, coo, x, L):
-    """Rows a..b-1 as a small CSR over the columns they reference (x gathered
-    and the column indices renumbered, so that only that part of x is sent to
-    the worker)."""
-    lo, hi = ip[a], ip[b]
-    cols = coo.col[lo:hi]
-    uniq, local = np.unique(cols, return_inverse=True)
-    data = np.zeros((L, hi - lo))
-    data[0] = coo.val[0, lo:hi]
-    return (ip[a:b + 1] - lo, local.astype(np.int32), data, np.ascontiguousarray(x[:, uniq]), L)
+class OracleSampler:
+    """The CPU oracle's SpMV timed on a bounded sample of the step's
+    matrices, one method for both bench arms.  Per (matrix, precision):
+    ``ncores`` slices of consecutive rows holding SLICE_ENTRIES[L] entries
+    each (about 50 ms of one core), starting at evenly spaced rows so the
+    sample spans the whole matrix (the power-law matrix's long rows sit
+    wherever the draw put them).  The matrices reach the worker processes as
+    .npy files mapped read-only from a temporary directory (no large
+    pickles, no shared-memory segment)."""
 
+    def __init__(self, mats, xs, ncores, slice_entries=None):
+        slice_entries = slice_entries or SLICE_ENTRIES
+        self.dir = tempfile.mkdtemp(prefix="mpspmv_oracle_")
+        self.ncores = ncores
+        self.tasks = {}
+        for mname, coo in mats.items():
+            ip = np.zeros(coo.nrows + 1, dtype=np.int64)
+            np.cumsum(np.bincount(coo.row, minlength=coo.nrows), out=ip[1:])
+            np.save(os.path.join(self.dir, mname + ".indptr.npy"), ip)
+            np.save(os.path.join(self.dir, mname + ".indices.npy"), coo.col.astype(np.int32))
+            np.save(os.path.join(self.dir, mname + ".vals.npy"), coo.val[0])
+            starts = [int(i * coo.nrows / ncores) for i in range(ncores)] + [coo.nrows]
+            for L in PRECS:
+                np.save(os.path.join(self.dir, "%s.x%d.npy" % (mname, L)), xs[mname][L])
+                tl = []
+                for i in range(ncores):
+                    a = starts[i]
+                    b = int(np.searchsorted(ip, ip[a] + slice_entries[L], side="left"))
+                    b = max(a + 1, min(b, starts[i + 1]))
+                    if a < coo.nrows:
+                        tl.append((self.dir, mname, L, a, b))
+                self.tasks[(mname, L)] = tl
+        self.desc = ("per (matrix, precision) %d slices of consecutive rows, each about %s entries (DD/TD/QD) and "
+                     "starting at evenly spaced rows, run at once on %d spawned processes (the slowest slice "
+                     "times the sample); rates combined with the GPU step's mix of entries"
+                     % (ncores, [SLICE_ENTRIES[L] for L in PRECS], ncores))
 
-def oracle_sample(mats, xs, entries_per_variant, pool, ncores):
-    """Oracle throughput on a sample: for every (matrix, precision) a block of
-    consecutive rows holding about entries_per_variant entries, cut into
-    ncores slices run in parallel.  xs[matrix][L] is the vector.  Returns
-    per-variant entries/s."""
-    rates = {}
-    for mname, coo in mats.items():
-        ip = np.zeros(coo.nrows + 1, dtype=np.int64)
-        np.add.at(ip, coo.row + 1, 1)
-        ip = np.cumsum(ip)
-        for L in PRECS:
-            want = entries_per_variant[L]
-            r0 = coo.nrows // 3
-            r1 = int(np.searchsorted(ip, ip[r0] + want))
-            r1 = max(r0 + 1, min(r1, coo.nrows))
-            bounds = np.linspace(r0, r1, ncores + 1).astype(np.int64)
-            tasks = [_task(ip, a, b, coo, xs[mname][L], L) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
-            # the slices run concurrently: the sample's time is the slowest one
-            dt = max(pool.map(_oracle_worker, tasks, chunksize=1))
-            rates[(mname, L)] = (ip[r1] - ip[r0]) / dt
-    return rates
+    def rates(self, pool):
+        """All-core entries/s per (matrix, L): the sample's entries over its
+        slowest slice (the slices run concurrently)."""
+        out = {}
+        for key, tl in self.tasks.items():
+            res = pool.map(_oracle_slice, tl, chunksize=1)
+            out[key] = sum(r[0] for r in res) / max(r[1] for r in res)
+        return out
+
+    def single_rates(self, pool):
+        """One-core entries/s per (matrix, L): the middle slice run alone."""
+        out = {}
+        for key, tl in self.tasks.items():
+            e, t = pool.apply(_oracle_slice, (tl[len(tl) // 2],))
+            out[key] = e / t
+        return out
+
+    def close(self):
+        shutil.rmtree(self.dir, ignore_errors=True)
 
 
 def cpu_rate_for_step(rates, nnz_of):
@@ -303,13 +349,16 @@ def run_reference(args):
     mats = make_matrices(args.small)
     xs = {m: {L: workloads.full_limb_vector(c.ncols, L, seed=0) for L in PRECS} for m, c in mats.items()}
     nnz_of = {(m, L): c.nnz for m, c in mats.items() for L in PRECS}
-    sample = {2: 400000, 3: 60000, 4: 60000}
+    sampler = OracleSampler(mats, xs, ncores)
     step_rates = []
-    with ctx.Pool(ncores) as pool:
-        for it in range(args.warmup + args.steps):
-            rates = oracle_sample(mats, xs, sample, pool, ncores)
-            if it >= args.warmup:
-                step_rates.append(cpu_rate_for_step(rates, nnz_of))
+    try:
+        with ctx.Pool(ncores) as pool:
+            for it in range(args.warmup + args.steps):
+                rates = sampler.rates(pool)
+                if it >= args.warmup:
+                    step_rates.append(cpu_rate_for_step(rates, nnz_of))
+    finally:
+        sampler.close()
     total_nnz = sum(nnz_of.values())
     ms = [total_nnz / r * 1e3 for r in step_rates]
     value = total_nnz / (sum(ms) / len(ms) * 1e-3) / 1e9
@@ -317,29 +366,26 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_block(mats),
+        "config": config_block(mats, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
-                         "sample": "per step and per (matrix, precision) a block of consecutive rows holding "
-                                   "%s entries, split over %d processes; time scaled to the full step" %
-                                   (sample, ncores)},
+                         "sample": sampler.desc + "; time scaled to one pass of the step's six products"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
-def config_block(mats):
-    return {"workload": "real CSR SpMV, DD/TD/QD P mode: " + ", ".join(
-        "%s (n=%d, nnz=%d)" % (k, v.nrows, v.nnz) for k, v in mats.items()),
-        "x": "every component random, seed 0", "l2": "flushed between timed steps (512 MiB write)",
-        "precisions": [PNAME[L] for L in PRECS]}
+def config_block(mats, repeat):
+    return {"workload": "real CSR SpMV y = A x in DD/TD/QD on binary64 matrix values (P-mode results: lower "
+                        "components zero; exact handles keep the one non-zero value plane and use the "
+                        "MP x binary64 product forms, bit-identical to full P storage): " + ", ".join(
+                            "%s (n=%d, nnz=%d)" % (k, v.nrows, v.nnz) for k, v in mats.items()),
+            "repeat_per_step": repeat,
+            "x": "every component random, seed 0",
+            "l2": "inputs larger than L2; also flushed between timed steps (512 MiB write)",
+            "precisions": [PNAME[L] for L in PRECS]}
 
 
-
-# ---------------------------------------------------------------------------
-# --suite: the other workloads (complex SpMV + BiCGSTAB, batched SpMM + CG,
-# learned selector).  Reported under "suite" in the JSON line.
-# ---------------------------------------------------------------------------
 def _time_events(fn, reps, stream):
     import torch
     evs = []
@@ -525,64 +571,210 @@ def suite_batched(mps, stream, small):
     return out
 
 
-def suite_selector(mps, small, flags=0):
-    """Learned precision selector on a scaled-down system set (360 systems,
-    n up to 160 rather than 1e4..1e5, so labelling stays within minutes):
-    SPD systems A = D (L L^T + I) D, n log-uniform in [40, 160], cond 10^U[8, 40],
-    labelled by the cheapest of binary64 / DD / TD / QD whose CG reaches
-    1e-30 within 30 n iterations; train on the first ones, evaluate on the
-    held-out rest against the plain ladder."""
-    from paper_2412_17510_gb300 import selector as sel
-    ntrain, ntest = (60, 20) if small else (300, 60)
-    rng = np.random.default_rng(0)
+def part_full_limb(mps, fp64_fma, hbm, stream, small, reps=10):
+    """Exact arithmetic on matrices whose values have L random components
+    (val_limbs = L, so every value plane is stored and the products take the
+    MP x MP forms): the QD products of the step's two matrices, Gnnz/s and
+    the three roofline fractions (the matrices are far larger than L2)."""
+    import torch
+    out = {}
+    L = 4
+    for mname, coo in make_matrices(small).items():
+        vals = workloads.full_limb_values(coo, L, seed=7)
+        h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, vals, L, mps.MPSPMV_EXACT_ACC,
+                                  val_limbs=L)
+        del vals
+        info = mps.mpspmv_get_info(h)
+        x = torch.from_numpy(workloads.full_limb_vector(coo.ncols, L, seed=0)).cuda()
+        y = torch.empty((L, coo.nrows), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            mps.mpspmv_spmv(h, x, y, stream)
+        ms = _time_events(lambda: mps.mpspmv_spmv(h, x, y, stream), reps, stream)
+        t = ms * 1e-3
+        nnz = info["nnz"]
+        tr = {"hbm": algorithmic_bytes(nnz, coo.nrows, coo.ncols, L, info["value_planes"]) / (hbm * 1e9),
+              "fp64": nnz * OPS_PER_ENTRY_EXACT[L] / fp64_fma,
+              "smem": nnz * UPD_PER_ENTRY_EXACT[L] / smem_peak_updates(2070.0)}
+        out["%s/QD" % mname] = {"ms": ms, "gnnz_s": nnz / t / 1e9, "value_planes": info["value_planes"],
+                                "roofline_frac": max(tr.values()) / t, "bound": max(tr, key=tr.get),
+                                "fracs": {k: v / t for k, v in tr.items()}}
+        mps.mpspmv_destroy(h)
+        del x, y
+    return out
+
+
+def roof_terms(arith, L, nnz, nrows, ncols, value_planes, fp64_fma, hbm):
+    """Roofline times (s) of one real product: HBM bytes, binary64 pipe,
+    shared-memory digit updates (exact arithmetic only)."""
+    if arith == "exact":
+        one = value_planes == 1
+        ops = (OPS_PER_ENTRY_EXACT_D if one else OPS_PER_ENTRY_EXACT)[L]
+        upd = (UPD_PER_ENTRY_EXACT_D if one else UPD_PER_ENTRY_EXACT)[L]
+    else:
+        ops, upd = OPS_PER_ENTRY[L], 0
+    return {"hbm": algorithmic_bytes(nnz, nrows, ncols, L, value_planes) / (hbm * 1e9),
+            "fp64": nnz * ops / fp64_fma, "smem": nnz * upd / smem_peak_updates(2070.0)}
+
+
+def part_powerlaw16(mps, fp64_fma, hbm, stream, small, reps=10):
+    """The power-law matrix with the mean row length the configuration
+    states (16): Zipf exponent 1.847 instead of 1.5, clipped to [1, 20000],
+    n = 1e6 (1e5 with --small), DD/TD/QD in both arithmetics."""
+    import torch
+    n = 100000 if small else 1000000
+    coo = workloads.power_law(n, s=1.847)
+    out = {"workload": "power-law n=%d, Zipf(1.847) clipped to [1, 20000], nnz=%d (mean %.1f per row)"
+                       % (n, coo.nnz, coo.nnz / n)}
+    for L in PRECS:
+        x = torch.from_numpy(workloads.full_limb_vector(n, L, seed=0)).cuda()
+        y = torch.empty((L, n), dtype=torch.float64, device="cuda")
+        for arith, fl in (("exact", mps.MPSPMV_EXACT_ACC), ("paper", 0)):
+            h = mps.mpspmv_create_csr(n, n, coo.row, coo.col, coo.val, L, fl, val_limbs=1)
+            info = mps.mpspmv_get_info(h)
+            for _ in range(3):
+                mps.mpspmv_spmv(h, x, y, stream)
+            ms = _time_events(lambda: mps.mpspmv_spmv(h, x, y, stream), reps, stream)
+            t = ms * 1e-3
+            tr = roof_terms(arith, L, info["nnz"], n, n, info["value_planes"], fp64_fma, hbm)
+            out["%s/%s" % (PNAME[L], arith)] = {"ms": ms, "gnnz_s": info["nnz"] / t / 1e9,
+                                                "roofline_frac": max(tr.values()) / t, "bound": max(tr, key=tr.get),
+                                                "fracs": {k: v / t for k, v in tr.items()}}
+            mps.mpspmv_destroy(h)
+        del x, y
+    return out
+
+
+def _selector_systems(sel, count, n_range, seed, flags):
+    rng = np.random.default_rng(seed)
     systems = []
-    for i in range(ntrain + ntest):
-        n = int(round(np.exp(rng.uniform(np.log(40), np.log(160)))))
-        coo, b = workloads.selector_system(n, float(rng.uniform(8, 40)), seed=1000 + i)
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        coo, b = workloads.selector_system(n, float(rng.uniform(8, 40)), seed=1000 * (seed + 1) + i)
         systems.append(sel.System(coo, b, flags))
-    t0 = time.perf_counter()
-    X = sel.features(systems)
-    y = sel.labels(systems, 1e-30, maxit_factor=30)
-    label_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    params, losses, _ = sel.train(X[:ntrain], y[:ntrain], epochs=300, batch=32, lr=0.05)
-    train_s = time.perf_counter() - t0
-    pred = sel.predict(params, X[ntrain:])
-    ev = sel.evaluate(systems[ntrain:], params, 1e-30, maxit_factor=30)
-    for s in systems:
-        s.free()
-    return {"systems": ntrain + ntest, "train": ntrain, "test": ntest,
-            "label_hist": {int(c): int((y == c).sum()) for c in range(5)},
-            "label_s": label_s, "train_s": train_s, "loss_first_last": [float(losses[0]), float(losses[-1])],
-            "test_accuracy": float((pred == y[ntrain:]).mean()),
-            "escalation_rate": ev["escalated"] / ev["n"],
-            "plain_ladder_s": ev["plain_s"], "selector_ladder_s": ev["auto_s"],
-            "batched_selector_s": ev["batched_auto_s"],
-            "solved": {"plain": ev["plain_ok"], "selector": ev["auto_ok"], "batched_selector": ev["batched_auto_ok"]}}
+    return systems
+
+
+def _selector_study(mps, ntrain, ntest, n_range, flags, per_system, seed=0, epochs=300):
+    """Selector study on SPD systems A = D (L L^T + I) D (cond 10^U[8, 40]):
+    labels from the method's own batched CG solves (cheapest of binary64 /
+    DD / TD / QD whose CG reaches 1e-30 within 30 n iterations), training by
+    the float32 kernels, then the held-out systems solved from x0 = 0 by the
+    plain ladder from every start level and by the selector (per system and
+    batched), every strategy timed end to end."""
+    from paper_2412_17510_gb300 import selector as sel
+    systems = _selector_systems(sel, ntrain + ntest, n_range, seed, flags)
+    try:
+        t0 = time.perf_counter()
+        X = sel.features(systems)
+        y = sel.labels(systems, 1e-30, maxit_factor=30)
+        label_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        params, losses, _ = sel.train(X[:ntrain], y[:ntrain], epochs=epochs, batch=32, lr=0.05)
+        train_s = time.perf_counter() - t0
+        pred = sel.predict(params, X[ntrain:])
+        ev = sel.evaluate(systems[ntrain:], params, 1e-30, maxit_factor=30, per_system=per_system)
+    finally:
+        for s in systems:
+            s.free()
+    out = {"systems": ntrain + ntest, "train": ntrain, "test": ntest, "n_range": list(n_range),
+           "label_hist": {PNAME.get(c + 1, "none"): int((y == c).sum()) for c in range(5)},
+           "label_s": label_s, "train_s": train_s, "loss_first_last": [float(losses[0]), float(losses[-1])],
+           "test_accuracy": float((pred == y[ntrain:]).mean()),
+           "batched": {"ladder_from_%s" % PNAME[L0]: v for L0, v in ev["batched_ladder"].items()}}
+    out["batched"]["selector"] = ev["batched_selector"]
+    if per_system:
+        out["per_system"] = {"ladder_from_%s" % PNAME[L0]: v for L0, v in ev["ladder"].items()}
+        sel_tot = dict(ev["selector"])
+        sel_tot.pop("final", None)
+        sel_tot["chosen_hist"] = {PNAME[c]: sel_tot["chosen"].count(c) for c in sorted(set(sel_tot["chosen"]))}
+        sel_tot.pop("chosen", None)
+        out["per_system"]["selector"] = sel_tot
+    return out
+
+
+def part_cg_time(mps, small):
+    """The metric's second half, CG time to a relative residual of 1e-30:
+    the plain precision ladder (binary64 -> DD -> TD -> QD, and constant
+    starts at DD, TD or QD) against the learned selector's choice, one
+    system after another and batched, on held-out systems (exact-
+    accumulation handles, n log-uniform in [40, 160])."""
+    ntrain, ntest = (60, 12) if small else (240, 24)
+    return _selector_study(mps, ntrain, ntest, (40, 160), mps.MPSPMV_EXACT_ACC, per_system=True)
+
+
+def suite_selector(mps, small, flags=0):
+    """Selector study with both arithmetics on 360 systems (n in [40, 160])."""
+    ntrain, ntest = (60, 20) if small else (300, 60)
+    return _selector_study(mps, ntrain, ntest, (40, 160), flags, per_system=True)
+
+
+def suite_selector_large(mps, small):
+    """The largest selector study that fits a bench run: 2,000 systems with n
+    log-uniform in [60, 400] (1,600 for training, 400 held out), exact
+    handles; the held-out comparison is batched only."""
+    ntrain, ntest = (200, 50) if small else (1600, 400)
+    return _selector_study(mps, ntrain, ntest, (60, 400), mps.MPSPMV_EXACT_ACC, per_system=False, seed=3)
+
+
+def suite_selector_scale(mps, small):
+    """CG iterations to 1e-30 against n on the selector's family (QD, exact
+    handles, cond 1e8 and 1e16, three systems each), with a cap of 100 n:
+    what rules out the configured n in [1e4, 1e5]."""
+    import torch
+    from paper_2412_17510_gb300 import selector as sel
+    out = {}
+    ns = (100, 300) if small else (100, 300, 1000, 3000)
+    for n in ns:
+        for lc in (8.0, 16.0):
+            rows = []
+            for k in range(3):
+                coo, b = workloads.selector_system(n, lc, seed=5000 + 10 * n + k)
+                s = sel.System(coo, b, mps.MPSPMV_EXACT_ACC)
+                try:
+                    x = torch.zeros((4, n), dtype=torch.float64, device="cuda")
+                    b4 = torch.zeros((4, n), dtype=torch.float64, device="cuda")
+                    b4[0] = s.b[0]
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    st, it, rr = mps.mpspmv_cg(s.handles[3], b4, x, 1e-30, 0.0, 100 * n)
+                    torch.cuda.synchronize()
+                    rows.append({"status": st, "iters": it, "iters_per_n": it / n, "relres": rr,
+                                 "s": time.perf_counter() - t0, "nnz": coo.nnz})
+                finally:
+                    s.free()
+            out["n=%d,cond=1e%d" % (n, lc)] = rows
+    return out
+
 
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+DEFAULT_PARTS = "complex,full_limb,powerlaw16,cg_time"
+SUITE_PARTS = "cg,product,batched,selector,selector_exact,selector_large,selector_scale"
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--repeat", type=int, default=8, help="passes over the six products per timed step")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced matrices (development)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle leg")
     ap.add_argument("--only", default=None, help="run one variant, e.g. powerlaw_1e5/QD (profiling)")
     ap.add_argument("--arith", default="both", choices=["paper", "exact", "both"],
                     help="paper: the paper's DD/TD/QD operation sequences; exact: error-free products on the "
-                         "binary64 pipe with exact integer accumulation (MPSPMV_EXACT_ACC); both: value from "
+                         "integer pipe with exact integer accumulation (MPSPMV_EXACT_ACC); both: value from "
                          "exact, the paper-order step timed too")
     ap.add_argument("--cg-only", default=None,
                     help="profiling: run only the CG workload of the suite in one variant, e.g. QD/exact, and exit")
     ap.add_argument("--cg-iters", type=int, default=200, help="CG iterations of the CG workload")
-    ap.add_argument("--suite", nargs="?", const="complex,cg,product,batched,selector,selector_exact", default=None,
-                    help="also measure the complex, CG, product-type, batched and selector workloads (adds "
-                         "minutes); "
-                         "optionally a comma-separated subset")
+    ap.add_argument("--parts", default=DEFAULT_PARTS,
+                    help="default-line parts after the timed step (comma-separated; 'none' for none)")
+    ap.add_argument("--suite", nargs="?", const=SUITE_PARTS, default=None,
+                    help="also measure the heavier workloads (CG, product-type methods, batched, selector "
+                         "studies; adds minutes); optionally a comma-separated subset")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -613,11 +805,11 @@ def main():
         print(json.dumps(out))
         return
 
+    R = max(1, args.repeat)
     mats = make_matrices(args.small)
     ariths = ["exact", "paper"] if args.arith == "both" else [args.arith]
     sets = {ar: [] for ar in ariths}
     xs_host = {}
-    xs_dev = {}
     for mname, coo in mats.items():
         xs_host[mname] = {L: workloads.full_limb_vector(coo.ncols, L, seed=0) for L in PRECS}
         for L in PRECS:
@@ -625,7 +817,6 @@ def main():
                 continue
             x = torch.from_numpy(xs_host[mname][L]).cuda()
             y = torch.empty((L, coo.nrows), dtype=torch.float64, device="cuda")
-            xs_dev[(mname, L)] = x
             for ar in ariths:
                 fl = mps.MPSPMV_EXACT_ACC if ar == "exact" else 0
                 h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, coo.val, L, fl, val_limbs=1)
@@ -639,18 +830,21 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(variants, evs=None):
-        for i, v in enumerate(variants):
-            if evs:
-                evs[i][0].record(stream)
-            mps.mpspmv_spmv(v["h"], v["x"], v["y"], stream)
-            if evs:
-                evs[i][1].record(stream)
+    def step(variants, evs=None, reps=1):
+        k = 0
+        for _ in range(reps):
+            for v in variants:
+                if evs:
+                    evs[k][0].record(stream)
+                mps.mpspmv_spmv(v["h"], v["x"], v["y"], stream)
+                if evs:
+                    evs[k][1].record(stream)
+                k += 1
 
-    def timed(variants, sample_clocks):
+    def timed(variants, sample_clocks, reps):
         for _ in range(args.warmup):
             flush.zero_()
-            step(variants)
+            step(variants, reps=reps)
         torch.cuda.synchronize()
         sampler = ClockSampler(local) if sample_clocks else None
         if sampler:
@@ -659,30 +853,36 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        all_evs = []
+        all_evs, step_evs = [], []
         for _ in range(args.steps):
             flush.zero_()
-            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in variants]
-            step(variants, evs)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(reps * len(variants))]
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            step(variants, evs, reps)
+            s1.record(stream)
             all_evs.append(evs)
+            step_evs.append((s0, s1))
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         clk = sampler.stop() if sampler else None
         per_var = np.zeros(len(variants))
-        step_ms = []
         for evs in all_evs:
-            t = [a.elapsed_time(b) for a, b in evs]
-            per_var += np.array(t)
-            step_ms.append(sum(t))
-        return per_var / args.steps, float(np.mean(step_ms)), clk
+            t = np.array([a.elapsed_time(b) for a, b in evs]).reshape(reps, len(variants))
+            per_var += t.sum(axis=0)
+        step_ms = [a.elapsed_time(b) for a, b in step_evs]
+        return per_var / (args.steps * reps), float(np.mean(step_ms)), clk
 
     primary = ariths[0]
     variants = sets[primary]
-    per_var, ms, clocks = timed(variants, True)
-    other = {ar: timed(sets[ar], False) for ar in ariths[1:]}
-    step_nnz = sum(v["nnz"] for v in variants)
+    per_var, ms, clocks = timed(variants, True, R)
+    # the paper-order step is about 17x slower: one pass per timed step
+    other = {ar: timed(sets[ar], False, 1) for ar in ariths[1:]}
+    step_nnz = R * sum(v["nnz"] for v in variants)
     ms, value = replica_value(ms, step_nnz, world, dist, device="cuda")
+
     def launches_of(v):
         i = v["info"]
         if v["arith"] != "exact":
@@ -692,9 +892,13 @@ def main():
             return inter + 1            # one row per thread
         return inter + 1 + (i["nsplit_rows"] > i["nlong_rows"]) + (i["nlong_rows"] > 0)
 
-    launches_per_step = sum(launches_of(v) for v in variants)
+    launches_per_step = R * sum(launches_of(v) for v in variants)
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # end to end through the host-buffer entry points (pinned host memory):
+    # every product copies its x in and its y out inside the timing; the
+    # products alternate between two streams, so one product's copies
+    # overlap another's kernels
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     e2e_ms = []
     h2d = d2h = 0
     hosts = []
@@ -702,21 +906,27 @@ def main():
         xh = torch.from_numpy(xs_host[v["m"]][v["L"]]).pin_memory()
         yh = torch.empty((v["L"], v["nrows"]), dtype=torch.float64).pin_memory()
         hosts.append((xh, yh))
-        h2d += xh.numel() * 8
-        d2h += yh.numel() * 8
+        h2d += R * xh.numel() * 8
+        d2h += R * yh.numel() * 8
+    torch.cuda.synchronize()
     for it in range(max(3, min(args.steps, 10)) + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for v, (xh, yh) in zip(variants, hosts):
-            mps.mpspmv_spmv_host(v["h"], xh, yh, stream)
+        for _ in range(R):
+            for i, (v, (xh, yh)) in enumerate(zip(variants, hosts)):
+                mps.mpspmv_spmv_host_async(v["h"], xh, yh, streams[i % 2])
+        for s_ in streams:
+            s_.synchronize()
         t1 = time.perf_counter()
         if it > 0:
             e2e_ms.append((t1 - t0) * 1e3)
     _, e2e_value = replica_value(float(np.mean(e2e_ms)), step_nnz, world, dist, device="cuda")
 
     hbm = 6786.2
+    hbm_src = "fallback 6786.2 GB/s (MEASURED_PEAKS.json absent)"
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        hbm_src = "MEASURED_PEAKS.json hbm_gbs"
     except Exception:
         pass
 
@@ -744,7 +954,8 @@ def main():
             t = pv[i] * 1e-3
             tr = times_of(w)
             out[w["name"]] = {"ms": pv[i], "gnnz_s": w["nnz"] / t / 1e9, "roofline_frac": max(tr.values()) / t,
-                              "bound": max(tr, key=tr.get), "fp64_tinstr_s": w["nnz"] * per_entry(w)[0] / t / 1e12,
+                              "bound": max(tr, key=tr.get), "fracs": {k: tr[k] / t for k in tr},
+                              "fp64_tinstr_s": w["nnz"] * per_entry(w)[0] / t / 1e12,
                               "hbm_gbs": bytes_of(w) / t / 1e9, "chunk": w["info"]["chunk"]}
         return out
 
@@ -766,12 +977,13 @@ def main():
                "(8-byte load + 8-byte store)" % (SMEM_BYTES_PER_CLK, UPD_BYTES))
     else:
         bound, achieved, peak, unit = "hbm", byts / t_s / 1e9, hbm, "GB/s"
-        src = "MEASURED_PEAKS.json hbm_gbs"
+        src = hbm_src
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
             "traffic": stored_traffic(v["arith"] + ":" + v["name"]),
             "kernel": "spmv run/row kernels + combine kernels, %s arithmetic, %s" % (v["arith"], v["name"]),
             "peak_source": src,
             "fracs": {k: tr[k] / t_s for k in tr},
+            "hbm_peak_source": hbm_src,
             "algorithmic_ops_per_launch": ops, "algorithmic_digit_updates_per_launch": upd,
             "algorithmic_bytes_per_launch": byts, "fp64_dadd_peak_tinstr_s": fp64_add / 1e12,
             "ops_per_entry": o_e, "updates_per_entry": u_e, "value_planes": v["info"]["value_planes"]}
@@ -779,7 +991,7 @@ def main():
     other_out = {}
     for ar, (pv, oms, _) in other.items():
         onnz = sum(w["nnz"] for w in sets[ar])
-        other_out[ar] = {"value": onnz / (oms * 1e-3) / 1e9, "ms_per_step": oms,
+        other_out[ar] = {"value": onnz / (oms * 1e-3) / 1e9, "ms_per_step": oms, "repeat_per_step": 1,
                          "breakdown": breakdown_of(sets[ar], pv)}
 
     # sampled rows of every variant's result, for the parity report of the
@@ -801,6 +1013,35 @@ def main():
         except Exception as e:  # the report is diagnostic: it never stops the measurement
             samples, parity = None, {"error": repr(e)}
 
+    for ar in ariths:
+        for w in sets[ar]:
+            mps.mpspmv_destroy(w["h"])
+    del hosts
+    parts_out = {}
+    if rank == 0:
+        del flush
+        torch.cuda.empty_cache()
+        parts = {"complex": lambda: suite_complex(mps, fp64_fma, hbm, stream, args.small),
+                 "full_limb": lambda: part_full_limb(mps, fp64_fma, hbm, stream, args.small),
+                 "powerlaw16": lambda: part_powerlaw16(mps, fp64_fma, hbm, stream, args.small),
+                 "cg_time": lambda: part_cg_time(mps, args.small),
+                 "cg": lambda: suite_cg(mps, stream, args.small),
+                 "product": lambda: suite_product(mps, stream, args.small),
+                 "batched": lambda: suite_batched(mps, stream, args.small),
+                 "selector": lambda: suite_selector(mps, args.small),
+                 "selector_exact": lambda: suite_selector(mps, args.small, mps.MPSPMV_EXACT_ACC),
+                 "selector_large": lambda: suite_selector_large(mps, args.small),
+                 "selector_scale": lambda: suite_selector_scale(mps, args.small)}
+        names = [] if args.parts in ("", "none") else args.parts.split(",")
+        if args.suite:
+            names += [p for p in args.suite.split(",") if p not in names]
+        for name in names:
+            if name not in parts:
+                raise SystemExit("unknown part %r" % name)
+            t0 = time.perf_counter()
+            parts_out[name] = parts[name]()
+            parts_out[name]["wall_s"] = time.perf_counter() - t0
+
     cpu = None
     if pool is not None:
         if samples is not None:
@@ -809,39 +1050,27 @@ def main():
             except Exception as e:
                 parity = {"error": repr(e)}
         nnz_of = {(w["m"], w["L"]): w["nnz"] for w in variants}
-        sample = {2: 4000000, 3: 500000, 4: 500000}
         t0 = time.perf_counter()
-        rates = oracle_sample(mats, xs_host, sample, pool, ncores)
+        sampler = OracleSampler(mats, xs_host, ncores)
+        try:
+            rates = sampler.rates(pool)
+            single = sampler.single_rates(pool)
+        finally:
+            sampler.close()
         cpu = {"value": cpu_rate_for_step(rates, nnz_of) / 1e9, "unit": UNIT, "cores": ncores, "kind": "oracle",
-               "sample": "per (matrix, precision) a block of consecutive rows holding %s entries (DD/TD/QD), split "
-                         "over %d spawned processes; rates combined with the GPU step's mix" % (sample, ncores),
+               "sample": sampler.desc, "single_core_value": cpu_rate_for_step(single, nnz_of) / 1e9,
+               "per_variant_all_cores": {"%s/%s" % (m, PNAME[L]): r / 1e9 for (m, L), r in rates.items()},
                "wall_s": time.perf_counter() - t0}
         pool.close()
 
-    for ar in ariths:
-        for w in sets[ar]:
-            mps.mpspmv_destroy(w["h"])
-    suite = None
-    if args.suite and rank == 0:
-        del flush
-        parts = {"complex": lambda: suite_complex(mps, fp64_fma, hbm, stream, args.small),
-                 "cg": lambda: suite_cg(mps, stream, args.small),
-                 "product": lambda: suite_product(mps, stream, args.small),
-                 "batched": lambda: suite_batched(mps, stream, args.small),
-                 "selector": lambda: suite_selector(mps, args.small),
-                 "selector_exact": lambda: suite_selector(mps, args.small, mps.MPSPMV_EXACT_ACC)}
-        suite = {}
-        for name in args.suite.split(","):
-            if name not in parts:
-                raise SystemExit("unknown suite part %r" % name)
-            suite[name] = parts[name]()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_block(mats),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_block(mats, R),
             "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "entry_point": "mpspmv_spmv_host_async, two streams, pinned host buffers"},
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "fp64_peak_tinstr_s": {"dfma": fp64_fma / 1e12, "dadd": fp64_add / 1e12},
             "arith": primary, "breakdown": breakdown,
@@ -850,8 +1079,13 @@ def main():
             line["other_arith"] = other_out
         if parity is not None:
             line["parity"] = parity
-        if suite is not None:
-            line["suite"] = suite
+        for name, res in parts_out.items():
+            key = {"complex": "complex", "full_limb": "full_limb_A", "powerlaw16": "powerlaw_mean16",
+                   "cg_time": "cg_time_to_1e-30"}.get(name)
+            if key:
+                line[key] = res
+            else:
+                line.setdefault("suite", {})[name] = res
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

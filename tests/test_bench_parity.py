@@ -73,3 +73,35 @@ def test_parity_report_catches_a_wrong_result():
     assert rep["exact_model_rows_bit_identical"] is False
     assert rep["max_bound_ratio"]["exact"]["powerlaw/QD"] > 1.0
     assert rep["max_bound_ratio"]["exact"]["stencil/DD"] == rep0["max_bound_ratio"]["exact"]["stencil/DD"]
+
+
+def test_oracle_sampler_slices_and_rates():
+    """The CPU baseline's sampler (one method for both bench arms): slices
+    start at evenly spaced rows, do not overlap, hold the requested entries
+    where the matrix allows, and the measured rates are the oracle's own
+    (a slice's product equals the oracle on the same rows)."""
+    import multiprocessing as mp
+    import bench  # by its own name: the spawned workers import the sampler's function from it
+    mats = {"powerlaw": workloads.power_law(3000, seed=3), "stencil": workloads.stencil_27pt(10)}
+    xs = {m: {L: workloads.full_limb_vector(c.ncols, L, seed=0) for L in bench.PRECS} for m, c in mats.items()}
+    want = {2: 5000, 3: 800, 4: 800}
+    sampler = bench.OracleSampler(mats, xs, 4, slice_entries=want)
+    try:
+        for (m, L), tl in sampler.tasks.items():
+            coo = mats[m]
+            ip = np.concatenate([[0], np.cumsum(np.bincount(coo.row, minlength=coo.nrows))])
+            assert len(tl) == 4
+            for i, (_, _, L2, a, b) in enumerate(tl):
+                assert L2 == L and a == int(i * coo.nrows / 4) and b > a
+                assert i == 3 or b <= tl[i + 1][3]
+                assert ip[b] - ip[a] >= min(want[L], ip[tl[i + 1][3] if i < 3 else coo.nrows] - ip[a]) or b == a + 1
+            e, t = bench._oracle_slice(tl[1])
+            assert e == ip[tl[1][4]] - ip[tl[1][3]] and t > 0
+        with mp.get_context("spawn").Pool(2) as pool:
+            rates = sampler.rates(pool)
+            single = sampler.single_rates(pool)
+        assert set(rates) == set(sampler.tasks) and all(r > 0 for r in rates.values())
+        assert all(r > 0 for r in single.values())
+    finally:
+        sampler.close()
+    assert not os.path.exists(sampler.dir)

@@ -66,6 +66,22 @@ def full_limb_vector(n, L, seed=0, cplx=False, rng=None):
     return out
 
 
+def full_limb_values(coo, L, seed=0):
+    """Matrix values with every component random: component 0 is the
+    matrix's own binary64 value, component k = U[-1,1] * 2**-53 * |component
+    k-1| (the rule of full_limb_vector).  Real matrices only; shape (L, nnz),
+    drawn in blocks to bound the temporaries."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((L, coo.nnz))
+    out[0] = coo.val[0]
+    step = 1 << 24
+    for a in range(0, coo.nnz, step):
+        b = min(a + step, coo.nnz)
+        for k in range(1, L):
+            out[k, a:b] = rng.uniform(-1.0, 1.0, b - a) * 2.0 ** -53 * np.abs(out[k - 1, a:b])
+    return out
+
+
 def integer_vector(n, L, lo=-8, hi=8, seed=0, cplx=False):
     """Integer-valued vector in component 0, zeros below."""
     rng = np.random.default_rng(seed)

@@ -53,17 +53,20 @@ PNAME = {1: "D", 2: "DD", 3: "TD", 4: "QD"}
 # components plus one folding addition each) -- the oracle's operation counts.
 OPS_PER_ENTRY = {2: 9 + 11, 3: 124 + 88, 4: 123 + 87}
 # exact accumulation (MPSPMV_EXACT_ACC): binary64 instructions per stored entry
-# -- only the FMA chain of the rounded products; the exact products are
-# formed on the integer pipe -- in P mode and on binary64 data (one stored
-# value plane, MP x binary64 product forms):
+# -- P mode (MP values): only the FMA chain of the rounded products, the
+# exact products are formed on the integer pipe; binary64 data (one stored
+# value plane): none, single-vector products take the wide-x form (x turned
+# once per product into a W-word fixed-point number per column, one integer
+# product a X per entry):
 OPS_PER_ENTRY_EXACT = {2: 2, 3: 3, 4: 4}
-OPS_PER_ENTRY_EXACT_D = {2: 1, 3: 1, 4: 1}
+OPS_PER_ENTRY_EXACT_D = {2: 0, 3: 0, 4: 0}
 # ... and shared-memory digit updates per stored entry, the accumulation's
-# own bound: an exact 106-bit product adds five 32-bit chunks, a rounded
-# binary64 term three (P mode: 1/3/6 exact products for DD/TD/QD; binary64
-# data: L - 1), each update an 8-byte load and an 8-byte store.
+# own bound: in P mode an exact 106-bit product adds five 32-bit chunks, a
+# rounded binary64 term three (1/3/6 exact products for DD/TD/QD); in the
+# wide-x form the product a X adds W + 2 chunks (W = 4/5/7 words); each
+# update an 8-byte load and an 8-byte store.
 UPD_PER_ENTRY_EXACT = {2: 8, 3: 18, 4: 33}
-UPD_PER_ENTRY_EXACT_D = {2: 8, 3: 13, 4: 18}
+UPD_PER_ENTRY_EXACT_D = {2: 6, 3: 7, 4: 9}
 SMEM_BYTES_PER_CLK = 128  # shared-memory bandwidth per SM per clock (32 banks x 4 B)
 UPD_BYTES = 16
 L2_FLUSH_BYTES = 512 << 20
@@ -323,12 +326,13 @@ def parity_report(mats, xs_host, rows_of, ysamp, chunk_of, sell_of=None):
                     bit_ok = bit_ok and bool(np.array_equal(y[:, one], ref[:, one]))
                     out["paper_one_run_rows"] += int(one.sum())
                 elif key[0] == "exact":
+                    # binary64 values: single-vector products take the wide-x
+                    # form, which the model follows step by step (every row)
                     whole = np.ones(len(rows), dtype=bool) if (sell_of or {}).get(key) else one
                     for i in np.nonzero(whole)[0]:
-                        want, fits = exact_model.row_model(L, 1, A, x, int(i))
-                        if fits:
-                            model_ok = model_ok and bool(np.array_equal(y[:, i], want))
-                            out["exact_model_rows"] += 1
+                        want, _ = exact_model.row_model_wide(L, A, x, int(i))
+                        model_ok = model_ok and bool(np.array_equal(y[:, i], want))
+                        out["exact_model_rows"] += 1
     if any(k[0] == "paper" for k in ysamp):
         out["paper_one_run_rows_bit_identical"] = bit_ok
     if out["exact_model_rows"]:

@@ -40,6 +40,7 @@ void free_handle(mpspmv_mat* h) {
   cudaFree(h->d_split);
   cudaFree(h->d_carry);
   cudaFree(h->d_xint);
+  cudaFree(h->d_xwide);
   cudaFree(h->d_slice_ptr);
   cudaFree(h->d_sell_cols);
   cudaFree(h->d_sell_vals);
@@ -255,7 +256,15 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
     TRY(dev_alloc(h, &h->d_vals, (int64_t)h->Pv * tlen));
     TRY(dev_alloc(h, &h->d_chunk_row, nchunks));
     TRY(dev_alloc(h, &h->d_split, h->nsplit));
-    if (h->exact && h->P > 1) TRY(dev_alloc(h, &h->d_xint, (int64_t)h->P * ncols));
+    if (h->exact && prec > 1 && h->Pv == V) {
+      // one value plane: single-vector products take the wide-x form, whose
+      // records (8 words per column part) replace the interleaved copy
+      double* xw = nullptr;
+      TRY(dev_alloc(h, &xw, (int64_t)V * 4 * ncols));
+      h->d_xwide = reinterpret_cast<uint32_t*>(xw);
+    } else if (h->exact && h->P > 1) {
+      TRY(dev_alloc(h, &h->d_xint, (int64_t)h->P * ncols));
+    }
     TRY(mps_ensure_carry(h, 1));
     if (cudaMemcpyAsync(h->d_indptr, indptr.data(), sizeof(int64_t) * (nrows + 1), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||

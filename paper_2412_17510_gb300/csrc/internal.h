@@ -61,6 +61,7 @@ struct mpspmv_mat {
   double* d_carry = nullptr;      // 2 * P * nchunks * carry_k
   int carry_k = 0;                // right-hand sides the carry buffer holds
   double* d_xint = nullptr;       // exact handles: x with the P components of a column adjacent
+  uint32_t* d_xwide = nullptr;    // exact handles with one value plane: the wide-x records of x (wide.cuh)
   // Exact handles with short, evenly sized rows: a sliced-ELL copy for
   // single-vector products (slices of 32 rows, entry q of row r at
   // slice_ptr[r / 32] + 32 q + r % 32), one thread per row.

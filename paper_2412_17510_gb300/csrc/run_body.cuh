@@ -122,6 +122,7 @@ __device__ __forceinline__ void process_run(const DevMat& m, int64_t c, int rhs,
 
 }  // namespace mpk
 #include "exact_prod.cuh"
+#include "wide.cuh"
 namespace mpk {
 
 // Operands of one stored entry, loaded ahead of their use.
@@ -278,6 +279,186 @@ __device__ __forceinline__ void process_row_exact(const DevMat& m, int64_t base,
   fas_to_mp<L, D, T>(sr, vr.v);
   if (CPLX) fas_to_mp<L, D, T>(si, vi.v);
   store_mp<L, CPLX>(y, ys, r * yoff, vr, vi);
+}
+
+// ---------------------------------------------------------------------------
+// Wide-x form (wide.cuh): single-vector products of exact handles with one
+// stored value plane.  xr points at the column records (8 words per column
+// part; complex: the real part's record, then the imaginary part's).
+// ---------------------------------------------------------------------------
+template <bool CPLX>
+__device__ __forceinline__ void load_rec(const uint32_t* __restrict__ xr, int64_t col, int part, uint32_t* rec) {
+  const uint4* q = reinterpret_cast<const uint4*>(xr + (col * (CPLX ? 2 : 1) + part) * kWideRecWords);
+  const uint4 u0 = __ldg(q), u1 = __ldg(q + 1);
+  rec[0] = u0.x; rec[1] = u0.y; rec[2] = u0.z; rec[3] = u0.w;
+  rec[4] = u1.x; rec[5] = u1.y; rec[6] = u1.z; rec[7] = u1.w;
+}
+
+// Software pipeline of a real entry stream (entry q at pos0 + 32 q): while
+// entry q is summed, the record of entry q + 1 is already being gathered and
+// the column and value of entry q + 2 loaded, so each thread keeps two
+// dependent gathers in flight instead of one.
+struct WidePipe {
+  uint32_t rec[kWideRecWords];  // record of the next entry
+  double a;                     // value of the next entry
+  int64_t col2;                 // column of the entry after it
+  double a2;                    // value of the entry after it
+};
+
+__device__ __forceinline__ void wide_pipe_start(const DevMat& m, int64_t pos0, int n, const uint32_t* __restrict__ xr,
+                                                WidePipe& pp) {
+  if (n > 0) {
+    pp.a = __ldg(m.vals + pos0);
+    load_rec<false>(xr, __ldg(m.cols + pos0), 0, pp.rec);
+  }
+  if (n > 1) {
+    pp.col2 = __ldg(m.cols + pos0 + 32);
+    pp.a2 = __ldg(m.vals + pos0 + 32);
+  }
+}
+
+__device__ __forceinline__ void wide_pipe_step(const DevMat& m, int64_t pos0, int q, int n,
+                                               const uint32_t* __restrict__ xr, WidePipe& pp, double& a,
+                                               uint32_t* rec) {
+  a = pp.a;
+#pragma unroll
+  for (int i = 0; i < kWideRecWords; i++) rec[i] = pp.rec[i];
+  if (q + 1 < n) {
+    pp.a = pp.a2;
+    load_rec<false>(xr, pp.col2, 0, pp.rec);
+  }
+  if (q + 2 < n) {
+    const int64_t pos = pos0 + 32 * (int64_t)(q + 2);
+    pp.col2 = __ldg(m.cols + pos);
+    pp.a2 = __ldg(m.vals + pos);
+  }
+}
+
+template <int L, bool CPLX, int D, int T>
+__device__ __forceinline__ void wide_entry(const DevMat& m, int64_t pos, const uint32_t* __restrict__ xr,
+                                           FixAccS<D, T>& sr, FixAccS<D, T>& si) {
+  const int64_t col = __ldg(m.cols + pos);
+  const double ar = __ldg(m.vals + pos);
+  uint32_t rec[kWideRecWords];
+  load_rec<CPLX>(xr, col, 0, rec);
+  fas_add_wide<L, D, T>(sr, ar, rec, false);
+  if (CPLX) {
+    const double ai = __ldg(m.vals + m.tlen + pos);
+    fas_add_wide<L, D, T>(si, ai, rec, false);   // a_im X_re
+    load_rec<CPLX>(xr, col, 1, rec);
+    fas_add_wide<L, D, T>(sr, ai, rec, true);    // - a_im X_im
+    fas_add_wide<L, D, T>(si, ar, rec, false);   // a_re X_im
+  }
+}
+
+// One row per thread from the sliced-ELL copy, wide-x form.
+template <int L, bool CPLX, int T>
+__device__ __forceinline__ void process_row_wide(const DevMat& m, int64_t base, int64_t r,
+                                                 const uint32_t* __restrict__ xr, double* __restrict__ y, int64_t ys) {
+  constexpr int D = Wide<L>::D;
+  __shared__ unsigned long long s_digits[(CPLX ? 4 : 2) * D * T];
+  FixAccS<D, T> sr, si;
+  sr.dp = s_digits + threadIdx.x;
+  sr.dn = s_digits + D * T + threadIdx.x;
+  si.dp = s_digits + (CPLX ? 2 * D * T : 0) + threadIdx.x;
+  si.dn = s_digits + (CPLX ? 3 * D * T : D * T) + threadIdx.x;
+  fas_reset<D, T>(sr);
+  if (CPLX) fas_reset<D, T>(si);
+  const int64_t len = __ldg(m.indptr + r + 1) - __ldg(m.indptr + r);
+  const int64_t slot0 = base + (r & 31);
+  if constexpr (CPLX) {
+#pragma unroll 1
+    for (int64_t q = 0; q < len; q++) wide_entry<L, CPLX, D, T>(m, slot0 + 32 * q, xr, sr, si);
+  } else {
+    WidePipe pp;
+    wide_pipe_start(m, slot0, (int)len, xr, pp);
+#pragma unroll 1
+    for (int q = 0; q < (int)len; q++) {
+      double a;
+      uint32_t rec[kWideRecWords];
+      wide_pipe_step(m, slot0, q, (int)len, xr, pp, a, rec);
+      fas_add_wide<L, D, T>(sr, a, rec, false);
+    }
+  }
+  mp<L> vr, vi = mp_zero<L>();
+  fas_to_mp<L, D, T>(sr, vr.v);
+  if (CPLX) fas_to_mp<L, D, T>(si, vi.v);
+  store_mp<L, CPLX>(y, ys, r, vr, vi);
+}
+
+// One run per thread, wide-x form: the run structure, carries and empty-row
+// handling of process_run_exact (single right-hand side).
+template <int L, bool CPLX, int T>
+__device__ __forceinline__ void process_run_wide(const DevMat& m, int64_t c, const uint32_t* __restrict__ xr,
+                                                 double* __restrict__ y, int64_t ys, double* __restrict__ carry,
+                                                 int kc) {
+  constexpr int P = CPLX ? 2 * L : L;
+  constexpr int D = Wide<L>::D;
+  __shared__ unsigned long long s_digits[(CPLX ? 4 : 2) * D * T];
+  const int64_t k0 = c * m.K;
+  const int64_t k1 = min(k0 + (int64_t)m.K, m.nnz);
+  int64_t row = __ldg(m.chunk_row + c);
+  const int64_t first_row = row;
+  const bool first_partial = __ldg(m.indptr + row) < k0;
+  int64_t rend = __ldg(m.indptr + row + 1);
+  const mp<L> z = mp_zero<L>();
+  if (c == 0) {
+    for (int64_t r = 0; r < row; r++) store_mp<L, CPLX>(y, ys, r, z, z);
+  }
+  FixAccS<D, T> sr, si;
+  sr.dp = s_digits + threadIdx.x;
+  sr.dn = s_digits + D * T + threadIdx.x;
+  si.dp = s_digits + (CPLX ? 2 * D * T : 0) + threadIdx.x;
+  si.dn = s_digits + (CPLX ? 3 * D * T : D * T) + threadIdx.x;
+  fas_reset<D, T>(sr);
+  if (CPLX) fas_reset<D, T>(si);
+  bool have = false;
+  const int n = (int)(k1 - k0);
+  const int64_t chunk_base = tile_pos(c, 0, m.K);
+  WidePipe pp;
+  if (!CPLX) wide_pipe_start(m, chunk_base, n, xr, pp);
+#pragma unroll 1
+  for (int j = 0; j < n; j++) {
+    if constexpr (CPLX) {
+      wide_entry<L, CPLX, D, T>(m, chunk_base + (int64_t)j * 32, xr, sr, si);
+    } else {
+      double a;
+      uint32_t rec[kWideRecWords];
+      wide_pipe_step(m, chunk_base, j, n, xr, pp, a, rec);
+      fas_add_wide<L, D, T>(sr, a, rec, false);
+    }
+    have = true;
+    const int64_t kk = k0 + j + 1;
+    if (kk == rend) {
+      mp<L> vr, vi = z;
+      fas_to_mp_to<L, D, T>(sr, vr.v);
+      if (CPLX) fas_to_mp_to<L, D, T>(si, vi.v);
+      if (row == first_row && first_partial) {
+#pragma unroll
+        for (int p = 0; p < P; p++) carry[((int64_t)p * m.nchunks + c) * kc] = p < L ? vr.v[p % L] : vi.v[p % L];
+      } else {
+        store_mp<L, CPLX>(y, ys, row, vr, vi);
+      }
+      fas_reset<D, T>(sr);
+      if (CPLX) fas_reset<D, T>(si);
+      have = false;
+      row++;
+      while (row < m.nrows && __ldg(m.indptr + row + 1) == kk) {
+        store_mp<L, CPLX>(y, ys, row, z, z);
+        row++;
+      }
+      rend = row < m.nrows ? __ldg(m.indptr + row + 1) : INT64_MAX;
+    }
+  }
+  if (have) {
+    mp<L> vr, vi = z;
+    fas_to_mp_to<L, D, T>(sr, vr.v);
+    if (CPLX) fas_to_mp_to<L, D, T>(si, vi.v);
+    const int w = (row == first_row && first_partial) ? 0 : 1;
+#pragma unroll
+    for (int p = 0; p < P; p++)
+      carry[((int64_t)(w * P + p) * m.nchunks + c) * kc] = p < L ? vr.v[p % L] : vi.v[p % L];
+  }
 }
 
 // Exact sum of the run partials of a row cut by run boundaries (exact-

@@ -254,6 +254,49 @@ __global__ void interleave_kernel(const double* __restrict__ x, int64_t n, int P
   xi[t] = x[(int64_t)p * n + col];
 }
 
+// Records of the wide-x form (wide.cuh): one thread per column part, the
+// real part's record then the imaginary part's.  Gated like the run kernel.
+template <int L, bool CPLX>
+__global__ void widen_kernel(const double* __restrict__ x, int64_t n, uint32_t* __restrict__ out, const int* gate) {
+  if (gate && *gate != 0) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  constexpr int parts = CPLX ? 2 : 1;
+  if (t >= n * parts) return;
+  const int64_t col = t / parts;
+  const int part = (int)(t - col * parts);
+  double c[L];
+#pragma unroll
+  for (int l = 0; l < L; l++) c[l] = x[(int64_t)(part * L + l) * n + col];
+  uint32_t rec[kWideRecWords];
+  wide_build<L>(c, rec);
+  uint4* o = reinterpret_cast<uint4*>(out + t * kWideRecWords);
+  o[0] = make_uint4(rec[0], rec[1], rec[2], rec[3]);
+  o[1] = make_uint4(rec[4], rec[5], rec[6], rec[7]);
+}
+
+// Wide-x form, one row per thread (sliced-ELL copy) and one run per thread.
+// The real kernels keep two gathers in flight per thread (software
+// pipeline, run_body.cuh) and hold more registers: 6 resident blocks.
+template <int L, bool CPLX>
+__global__ void __launch_bounds__(kThreads, CPLX ? 3 : 6)
+    sell_wide_kernel(DevMat m, const int64_t* __restrict__ slice_ptr, const uint32_t* __restrict__ xw,
+                     double* __restrict__ y, int64_t ys, const int* __restrict__ gate) {
+  if (gate && *gate != 0) return;
+  const int64_t r = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (r >= m.nrows) return;
+  process_row_wide<L, CPLX, kThreads>(m, __ldg(slice_ptr + (r >> 5)), r, xw, y, ys);
+}
+
+template <int L, bool CPLX>
+__global__ void __launch_bounds__(kThreads, CPLX ? 3 : 6)
+    spmv_runs_wide_kernel(DevMat m, const uint32_t* __restrict__ xw, double* __restrict__ y, int64_t ys,
+                          double* __restrict__ carry, int kc, const int* __restrict__ gate) {
+  if (gate && *gate != 0) return;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= m.nchunks) return;
+  process_run_wide<L, CPLX, kThreads>(m, c, xw, y, ys, carry, kc);
+}
+
 // y = 0 (single right-hand side), gated
 __global__ void zero_kernel(double* y, int64_t ys, int64_t yoff, int64_t nrows, int P, const int* gate) {
   if (gate && *gate != 0) return;
@@ -262,6 +305,10 @@ __global__ void zero_kernel(double* y, int64_t ys, int64_t yoff, int64_t nrows, 
   const int64_t p = t / nrows, r = t - p * nrows;
   y[p * ys + r * yoff] = 0.0;
 }
+
+template <int L, bool CPLX>
+int launch_combine(const mpspmv_mat* h, const DevMat& m, double* y, int64_t ys, int64_t yoff, int k, const int* gate,
+                   cudaStream_t s);
 
 template <int L, bool CPLX, bool MIXED>
 int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, double* y, int64_t ys,
@@ -287,6 +334,30 @@ int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, d
   }
   int kp = 1;
   while (kp < k) kp <<= 1;
+  if constexpr (MIXED && L > 1) {
+    if (h->d_xwide && k == 1 && xoff == 1 && yoff == 1) {  // single vector, wide-x form
+      const int64_t tot = (int64_t)(CPLX ? 2 : 1) * h->ncols;
+      if (tot > 0) {
+        widen_kernel<L, CPLX><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(x, xs, h->d_xwide,
+                                                                                          gate);
+        MPS_CUDA(cudaGetLastError());
+      }
+      if (h->sell_len > 0) {
+        DevMat ms = m;
+        ms.cols = h->d_sell_cols;
+        ms.vals = h->d_sell_vals;
+        ms.tlen = h->sell_len;
+        sell_wide_kernel<L, CPLX><<<(unsigned)((h->nrows + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            ms, h->d_slice_ptr, h->d_xwide, y, ys, gate);
+        MPS_CUDA(cudaGetLastError());
+        return MPSPMV_OK;
+      }
+      spmv_runs_wide_kernel<L, CPLX><<<(unsigned)((h->nchunks + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+          m, h->d_xwide, y, ys, h->d_carry, h->carry_k, gate);
+      MPS_CUDA(cudaGetLastError());
+      return launch_combine<L, CPLX>(h, m, y, ys, yoff, k, gate, s);
+    }
+  }
   if (h->exact && k == 1 && h->d_xint) {  // single vector: gather from the interleaved copy
     const int64_t tot = (int64_t)h->P * h->ncols;
     interleave_kernel<<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(x, h->ncols, h->P, h->d_xint,
@@ -315,6 +386,13 @@ int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, d
     spmv_runs_kernel<L, CPLX, MIXED, false><<<(unsigned)blocks, kThreads, 0, s>>>(m, x, xs, xoff, y, ys, yoff,
                                                                                h->d_carry, h->carry_k, kp, k, gate);
   MPS_CUDA(cudaGetLastError());
+  return launch_combine<L, CPLX>(h, m, y, ys, yoff, k, gate, s);
+}
+
+// Rows cut by run boundaries: the combine kernels over the carry buffer.
+template <int L, bool CPLX>
+int launch_combine(const mpspmv_mat* h, const DevMat& m, double* y, int64_t ys, int64_t yoff, int k, const int* gate,
+                   cudaStream_t s) {
   if (h->nshort > 0) {
     const int64_t ct = h->nshort * k;
     const unsigned nb = (unsigned)((ct + kThreads - 1) / kThreads);

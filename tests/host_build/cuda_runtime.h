@@ -6,6 +6,7 @@
 // the high half of a 64 x 64-bit product, count of leading zeros, and the
 // classification functions the device code calls unqualified.
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -39,3 +40,5 @@ using std::isinf;
 using std::isnan;
 using std::isfinite;
 using std::scalbn;
+using std::max;
+using std::min;

@@ -15,6 +15,7 @@
 #include "exact_prod.cuh"
 #undef volatile
 #undef asm
+#include "wide.cuh"
 
 namespace {
 
@@ -213,9 +214,107 @@ void flush(const unsigned long long* dp_in, const unsigned long long* dn_in, int
   mpk::fas_to_mp<L, D, 1>(acc, out);
 }
 
+// wide-x form: the record of one column part, and a row of n entries (a[i]
+// binary64, X + i L the components of the x it multiplies) summed in the
+// row accumulator of that form and cut to L components
+template <int L>
+void wide_rec(const double* c, uint32_t* rec) {
+  mpk::wide_build<L>(c, rec);
+}
+
+template <int L>
+void wide_row(int n, const double* a, const double* X, double* out) {
+  constexpr int D = mpk::Wide<L>::D;
+  unsigned long long dp[D], dn[D];
+  mpk::FixAccS<D, 1> acc;
+  acc.dp = dp;
+  acc.dn = dn;
+  mpk::fas_reset<D, 1>(acc);
+  for (int i = 0; i < n; i++) {
+    uint32_t rec[mpk::kWideRecWords];
+    mpk::wide_build<L>(X + (int64_t)i * L, rec);
+    mpk::fas_add_wide<L, D, 1>(acc, a[i], rec, false);
+  }
+  mpk::fas_to_mp<L, D, 1>(acc, out);
+}
+
+// complex row in the kernels' order: re += a_re X_re, im += a_im X_re,
+// re -= a_im X_im, im += a_re X_im
+template <int L>
+void wide_row_c(int n, const double* ar, const double* ai, const double* Xr, const double* Xi, double* out_re,
+                double* out_im) {
+  constexpr int D = mpk::Wide<L>::D;
+  unsigned long long dp[2][D], dn[2][D];
+  mpk::FixAccS<D, 1> sr, si;
+  sr.dp = dp[0];
+  sr.dn = dn[0];
+  si.dp = dp[1];
+  si.dn = dn[1];
+  mpk::fas_reset<D, 1>(sr);
+  mpk::fas_reset<D, 1>(si);
+  for (int i = 0; i < n; i++) {
+    uint32_t rr[mpk::kWideRecWords], ri[mpk::kWideRecWords];
+    mpk::wide_build<L>(Xr + (int64_t)i * L, rr);
+    mpk::wide_build<L>(Xi + (int64_t)i * L, ri);
+    mpk::fas_add_wide<L, D, 1>(sr, ar[i], rr, false);
+    mpk::fas_add_wide<L, D, 1>(si, ai[i], rr, false);
+    mpk::fas_add_wide<L, D, 1>(sr, ai[i], ri, true);
+    mpk::fas_add_wide<L, D, 1>(si, ar[i], ri, false);
+  }
+  mpk::fas_to_mp<L, D, 1>(sr, out_re);
+  mpk::fas_to_mp<L, D, 1>(si, out_im);
+}
+
 }  // namespace
 
 extern "C" {
+
+int host_wide_rec(int L, const double* c, uint32_t* rec) {
+  switch (L) {
+    case 2: wide_rec<2>(c, rec); return 0;
+    case 3: wide_rec<3>(c, rec); return 0;
+    case 4: wide_rec<4>(c, rec); return 0;
+    default: return -1;
+  }
+}
+
+int host_wide_row(int L, int n, const double* a, const double* X, double* out) {
+  switch (L) {
+    case 2: wide_row<2>(n, a, X, out); return 0;
+    case 3: wide_row<3>(n, a, X, out); return 0;
+    case 4: wide_row<4>(n, a, X, out); return 0;
+    default: return -1;
+  }
+}
+
+int host_wide_row_c(int L, int n, const double* ar, const double* ai, const double* Xr, const double* Xi,
+                    double* out_re, double* out_im) {
+  switch (L) {
+    case 2: wide_row_c<2>(n, ar, ai, Xr, Xi, out_re, out_im); return 0;
+    case 3: wide_row_c<3>(n, ar, ai, Xr, Xi, out_re, out_im); return 0;
+    case 4: wide_row_c<4>(n, ar, ai, Xr, Xi, out_re, out_im); return 0;
+    default: return -1;
+  }
+}
+
+int host_wide_digits(int L) {
+  switch (L) {
+    case 2: return mpk::Wide<2>::D;
+    case 3: return mpk::Wide<3>::D;
+    case 4: return mpk::Wide<4>::D;
+    default: return -1;
+  }
+}
+
+int host_wide_words(int L) {
+  switch (L) {
+    case 2: return mpk::Wide<2>::W;
+    case 3: return mpk::Wide<3>::W;
+    case 4: return mpk::Wide<4>::W;
+    default: return -1;
+  }
+}
+
 
 int host_row_sum(int L, int mode, int n, const double* A, const double* X, double* out) {
   switch (L) {

@@ -37,7 +37,7 @@ def _setup(bench):
                              np.concatenate([A.indices[A.indptr[r]:A.indptr[r + 1]] for r in rows]),
                              np.concatenate([A.data[:, A.indptr[r]:A.indptr[r + 1]] for r in rows], axis=1), L,
                              False)
-            ysamp[("exact", m, L)] = np.stack([em.row_model(L, 1, sub, xs[m][L], i)[0] for i in range(len(rows))],
+            ysamp[("exact", m, L)] = np.stack([em.row_model_wide(L, sub, xs[m][L], i)[0] for i in range(len(rows))],
                                               axis=1)
             chunk_of[("paper", m, L)] = chunk_of[("exact", m, L)] = 64
     return mats, xs, rows_of, ysamp, chunk_of

@@ -146,11 +146,13 @@ def test_stencil_full_size_sampled_rows():
 
 @pytest.mark.parametrize("L", [2, 3, 4])
 @pytest.mark.parametrize("cplx", [False, True])
-def test_binary64_storage_is_bit_identical(L, cplx):
-    """Exact accumulation on binary64 data stores the leading components only
-    and uses the MP x binary64 product forms; the products it leaves out are
-    exactly zero, so the result equals that of the full P-mode storage (the
-    same values passed with explicit zero lower components) bit for bit."""
+def test_binary64_storage_forms(L, cplx):
+    """Exact accumulation on binary64 data stores the leading components
+    only.  Its multi-right-hand-side products use the MP x binary64 forms,
+    whose left-out products are exactly zero, so they equal those of the
+    full P-mode storage (the same values passed with explicit zero lower
+    components) bit for bit; its single-vector products take the wide-x
+    form, which meets the same bound."""
     coo = workloads.random_sparse(700, 650, 40, seed=30 + L, cplx=cplx, empty_frac=0.1)
     fl = EX | (1 if cplx else 0)
     h1 = mps.mpspmv_create_csr(700, 650, coo.row, coo.col, coo.val, L, fl, val_limbs=1)
@@ -160,11 +162,18 @@ def test_binary64_storage_is_bit_identical(L, cplx):
         assert mps.mpspmv_get_info(h2)["value_planes"] == (2 * L if cplx else L)
         P = 2 * L if cplx else L
         x = workloads.full_limb_vector(650, L, seed=8, cplx=cplx)
-        y1 = gpu_spmv(h1, x, P, 700)
-        y2 = gpu_spmv(h2, x, P, 700)
-        assert np.array_equal(y1, y2)
+        X = np.ascontiguousarray(np.stack([x, x], axis=-1))
+        Ys = []
+        for h in (h1, h2):
+            Yd = torch.empty((P, 700, 2), dtype=torch.float64, device="cuda")
+            mps.mpspmv_spmm(h, 2, to_dev(X), 2, Yd, 2)
+            torch.cuda.synchronize()
+            Ys.append(Yd.cpu().numpy())
+        assert np.array_equal(Ys[0], Ys[1])
         A = oracle.coo_to_csr(700, 650, coo.row, coo.col, coo.promoted(L), L, cplx)
+        y1 = gpu_spmv(h1, x, P, 700)
         assert exact.bound_ratio(y1, A, x) <= 1.0
+        assert exact.bound_ratio(Ys[0][:, :, 0], A, x) <= 1.0
     finally:
         mps.mpspmv_destroy(h1)
         mps.mpspmv_destroy(h2)
@@ -266,14 +275,16 @@ def _model_case(L, layout, mode, cplx):
 @pytest.mark.parametrize("cplx", [False, True])
 def test_rows_bit_identical_to_the_exact_model(L, layout, mode, cplx):
     """Rows that one thread sums end to end equal the exact model bit for bit
-    (oracle/exact_model.py): the exact sum of the entries' decomposed terms
-    (exact products below the unit roundoff plus one FMA chain; complex data
-    in the pattern re += a_re x_re - a_im x_im, im += a_re x_im + a_im x_re),
-    cut to L components by truncation -- for every row whose terms fit the
-    window.  Layouts: the row-per-thread copy of a 27-point stencil (every
-    row) and the run layout of short random rows (the rows inside one run).
-    Values: MP (every component random, mode 0) or binary64 (leading
-    component stored, mode 1)."""
+    (oracle/exact_model.py).  MP values (every component random, mode 0):
+    the exact sum of the entries' decomposed terms (exact products below the
+    unit roundoff plus one FMA chain), cut to L components by truncation,
+    for every row whose terms fit the window.  Binary64 values (leading
+    component stored, mode 1): the wide-x form (x turned into one W-word
+    fixed-point number per column, one product a X per entry), the model
+    following the row accumulator step by step, for every row.  Complex data
+    in the pattern re += a_re x_re - a_im x_im, im += a_re x_im + a_im x_re.
+    Layouts: the row-per-thread copy of a 27-point stencil (every row) and
+    the run layout of short random rows (the rows inside one run)."""
     coo, A, vals, limbs = _model_case(L, layout, mode, cplx)
     P = 2 * L if cplx else L
     h = mps.mpspmv_create_csr(coo.nrows, coo.ncols, coo.row, coo.col, vals, L,
@@ -292,8 +303,65 @@ def test_rows_bit_identical_to_the_exact_model(L, layout, mode, cplx):
         rows = unsplit_rows(A, info["chunk"])
     compared = 0
     for r in rows:
-        want, fits = model.row_model(L, mode, A, x, int(r))
+        if mode == 1:
+            want, fits = model.row_model_wide(L, A, x, int(r))
+            fits = True
+        else:
+            want, fits = model.row_model(L, mode, A, x, int(r))
         if fits:
             assert np.array_equal(y[:, r], want), (L, layout, mode, cplx, int(r), y[:, r], want)
             compared += 1
     assert compared >= max(100, len(rows) // 2)
+    if mode == 1:
+        assert compared == len(rows)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_wide_form_edge_cases(L):
+    """Wide-x form on binary64 data: x with zero, subnormal, cancelling,
+    overflowing and non-finite columns; entries far below a row's largest
+    (the truncating path below the window) and window moves; empty rows.
+    Rows that one run holds equal the model bit for bit (rows cut by runs are
+    combined from their runs' L-component partials); every row that
+    references a non-finite x is NaN; the rest meet the bound."""
+    rng = np.random.default_rng(90 + L)
+    n, ncols = 600, 64
+    near, _ = _near_uniform(n, ncols, 7, 8, 0.03, seed=91 + L, cplx=False, L=1)
+    coo = workloads.COO(n, ncols, near.row, near.col, rng.standard_normal((1, near.nnz)))
+    vals = coo.val.copy()
+    vals[0, ::5] *= 2.0 ** rng.integers(-300, 300, vals[0, ::5].shape[0])
+    coo = workloads.COO(n, ncols, coo.row, coo.col, vals)
+    x = workloads.full_limb_vector(ncols, L, seed=92 + L)
+    x[:, 3] = 0.0
+    x[:, 5] = 0.0
+    x[L - 1, 5] = 2.0 ** -1070
+    x[1, 7] = -x[0, 7]
+    x[0, 9] = float("inf")
+    x[:, 11] *= 2.0 ** 900
+    A = oracle.coo_to_csr(n, ncols, coo.row, coo.col, coo.promoted(L), L)
+    h = mps.mpspmv_create_csr(n, ncols, coo.row, coo.col, coo.val, L, EX, val_limbs=1)
+    try:
+        info = mps.mpspmv_get_info(h)
+        y = gpu_spmv(h, x, L, n)
+    finally:
+        mps.mpspmv_destroy(h)
+    assert info["sell_slots"] > 0  # short, even rows: one row per thread, every row compared
+    one = set(range(n))
+    compared = 0
+    finite = []
+    for r in range(n):
+        want, _ = model.row_model_wide(L, A, x, r)
+        if np.isnan(want[0]):
+            assert np.isnan(y[0, r])
+        elif r in one:
+            assert np.array_equal(y[:, r], want), (L, r, y[:, r], want)
+            compared += 1
+        # the bound needs results whose L components lie in the normal range
+        # (a subnormal result cannot carry them)
+        if np.isfinite(want).all() and (want[0] == 0.0 or abs(want[0]) > 2.0 ** -800):
+            finite.append(r)
+    assert compared >= n // 2
+    assert not y[:, np.diff(A.indptr) == 0].any()
+    xb = x.copy()
+    xb[:, 9] = 0.0  # the rows checked do not reference the non-finite column
+    assert exact.bound_ratio(y[:, finite], A, xb, rows=finite) <= 1.0

@@ -477,3 +477,118 @@ def test_axpy_elements_equal_the_exact_model(lib, L, cplx):
         assert np.array_equal(out, want), (L, cplx, i)
         checked += 1
     assert checked >= n // 2
+
+
+# ---------------------------------------------------------------------------
+# wide-x form (csrc/wide.cuh) against the model's wide_record / row_model_wide
+# ---------------------------------------------------------------------------
+def _wide_lib(lib):
+    _u32 = ctypes.POINTER(ctypes.c_uint32)
+    lib.host_wide_rec.argtypes = [ctypes.c_int, _dp, _u32]
+    lib.host_wide_row.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+    lib.host_wide_row_c.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    for L in (2, 3, 4):
+        assert lib.host_wide_words(L) == model.WIDE_WORDS[L]
+        assert lib.host_wide_digits(L) == model.WIDE_DIGITS[L]
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _host_record(lib, c, L):
+    w = np.zeros(8, dtype=np.uint32)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    lib.host_wide_rec(L, _dptr(c), w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    meta = int(w[7])
+    if meta & 1:
+        return None
+    W = model.WIDE_WORDS[L]
+    M = sum(int(w[i]) << (32 * i) for i in range(W))
+    if M == 0:
+        return 0, 0, 0
+    E = ctypes.c_int32(meta).value >> 2
+    return (-1 if meta & 2 else 1), M, E
+
+
+def _wide_x_cases(L, rng, n):
+    """Column components of many kinds: full-limb values over the exponent
+    range, lower components of either sign, overlapping (non-canonical)
+    components, exact cancellation, zeros, subnormals, gaps wider than the
+    record's window."""
+    out = []
+    for i in range(n):
+        x = workloads.full_limb_vector(1, L, rng=rng)[:, 0] * 2.0 ** int(rng.integers(-1000, 1000))
+        k = i % 8
+        if k == 1:
+            x[1:] = -x[1:]
+        elif k == 2:
+            x[1] = x[0] * float(rng.uniform(-0.9, 0.9))                 # overlapping
+        elif k == 3:
+            x[1] = -x[0]                                                # cancellation
+        elif k == 4:
+            x[:] = 0.0
+            x[L - 1] = float(rng.uniform(-1, 1)) * 2.0 ** -1070         # subnormal only
+        elif k == 5:
+            x[L - 1] = x[0] * 2.0 ** -400                               # beyond the window
+        elif k == 6:
+            x[0] = 0.0
+        out.append(x)
+    return out
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_wide_records_equal_the_model(lib, L):
+    """The record the kernels build for a column equals the model's
+    (s, M, E) for 2,400 columns of every kind, and non-finite components give
+    the NaN record."""
+    h = _wide_lib(lib)
+    rng = np.random.default_rng(300 + L)
+    for x in _wide_x_cases(L, rng, 2400):
+        assert _host_record(h, x, L) == model.wide_record(x, L), x
+    x = np.zeros(L)
+    x[0] = float("inf")
+    assert _host_record(h, x, L) is None
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_wide_rows_equal_the_model(lib, L, cplx):
+    """Rows of the wide form (records built per entry, products added in the
+    row accumulator, cut to L components) equal the model bit for bit --
+    the model follows the accumulator's window moves and truncations step by
+    step -- and meet the bound 8 m u (|A||x|): rows of 1-40 entries with
+    binary64 values over narrow and wide spreads of exponents."""
+    h = _wide_lib(lib)
+    rng = np.random.default_rng(400 + L + (10 if cplx else 0))
+    compared = 0
+    for i in range(400):
+        n = int(rng.integers(1, 41))
+        spread = 10 if i % 2 else 200
+        ar = rng.standard_normal(n) * 2.0 ** rng.integers(-spread, spread + 1, n)
+        ai = rng.standard_normal(n) * 2.0 ** rng.integers(-spread, spread + 1, n)
+        xr = np.stack([workloads.full_limb_vector(1, L, rng=rng)[:, 0] * 2.0 ** int(rng.integers(-spread, spread + 1))
+                       for _ in range(n)])
+        xi = np.stack([workloads.full_limb_vector(1, L, rng=rng)[:, 0] * 2.0 ** int(rng.integers(-spread, spread + 1))
+                       for _ in range(n)])
+        V = 2 if cplx else 1
+        vals = np.zeros((V * L, n))
+        vals[0] = ar
+        if cplx:
+            vals[L] = ai
+        A = oracle.CSR(1, n, np.array([0, n]), np.arange(n, dtype=np.int32), vals, L, cplx)
+        x = np.concatenate([xr.T, xi.T]) if cplx else xr.T
+        want, fits = model.row_model_wide(L, A, x, 0)
+        if cplx:
+            ore, oim = np.zeros(L), np.zeros(L)
+            h.host_wide_row_c(L, n, _dptr(ar), _dptr(ai), _dptr(np.ascontiguousarray(xr)),
+                              _dptr(np.ascontiguousarray(xi)), _dptr(ore), _dptr(oim))
+            got = np.concatenate([ore, oim])
+        else:
+            got = np.zeros(L)
+            h.host_wide_row(L, n, _dptr(ar), _dptr(np.ascontiguousarray(xr)), _dptr(got))
+        assert np.array_equal(got, want), (i, got, want)
+        compared += 1
+        assert exact.bound_ratio(got[:, None], A, x) <= 1.0
+    assert compared == 400

@@ -295,42 +295,56 @@ __device__ __forceinline__ void load_rec(const uint32_t* __restrict__ xr, int64_
 }
 
 // Software pipeline of a real entry stream (entry q at pos0 + 32 q): while
-// entry q is summed, the record of entry q + 1 is already being gathered and
-// the column and value of entry q + 2 loaded, so each thread keeps two
-// dependent gathers in flight instead of one.
+// entry q is summed, the records of entries q + 1 .. q + kWideDepth are
+// already being gathered and the column and value of the entry after them
+// loaded, so each thread keeps kWideDepth dependent gathers in flight
+// instead of one.
+constexpr int kWideDepth = 1;
+
 struct WidePipe {
-  uint32_t rec[kWideRecWords];  // record of the next entry
-  double a;                     // value of the next entry
-  int64_t col2;                 // column of the entry after it
-  double a2;                    // value of the entry after it
+  uint32_t rec[kWideDepth][kWideRecWords];  // records of the next entries
+  double a[kWideDepth];                     // their values
+  int64_t coln;                             // column of the entry after them
+  double an;                                // its value
 };
 
 __device__ __forceinline__ void wide_pipe_start(const DevMat& m, int64_t pos0, int n, const uint32_t* __restrict__ xr,
                                                 WidePipe& pp) {
-  if (n > 0) {
-    pp.a = __ldg(m.vals + pos0);
-    load_rec<false>(xr, __ldg(m.cols + pos0), 0, pp.rec);
+#pragma unroll
+  for (int i = 0; i < kWideDepth; i++) {
+    if (i < n) {
+      const int64_t pos = pos0 + 32 * (int64_t)i;
+      pp.a[i] = __ldg(m.vals + pos);
+      load_rec<false>(xr, __ldg(m.cols + pos), 0, pp.rec[i]);
+    }
   }
-  if (n > 1) {
-    pp.col2 = __ldg(m.cols + pos0 + 32);
-    pp.a2 = __ldg(m.vals + pos0 + 32);
+  if (kWideDepth < n) {
+    const int64_t pos = pos0 + 32 * (int64_t)kWideDepth;
+    pp.coln = __ldg(m.cols + pos);
+    pp.an = __ldg(m.vals + pos);
   }
 }
 
 __device__ __forceinline__ void wide_pipe_step(const DevMat& m, int64_t pos0, int q, int n,
                                                const uint32_t* __restrict__ xr, WidePipe& pp, double& a,
                                                uint32_t* rec) {
-  a = pp.a;
+  a = pp.a[0];
 #pragma unroll
-  for (int i = 0; i < kWideRecWords; i++) rec[i] = pp.rec[i];
-  if (q + 1 < n) {
-    pp.a = pp.a2;
-    load_rec<false>(xr, pp.col2, 0, pp.rec);
+  for (int w = 0; w < kWideRecWords; w++) rec[w] = pp.rec[0][w];
+#pragma unroll
+  for (int i = 0; i + 1 < kWideDepth; i++) {
+    pp.a[i] = pp.a[i + 1];
+#pragma unroll
+    for (int w = 0; w < kWideRecWords; w++) pp.rec[i][w] = pp.rec[i + 1][w];
   }
-  if (q + 2 < n) {
-    const int64_t pos = pos0 + 32 * (int64_t)(q + 2);
-    pp.col2 = __ldg(m.cols + pos);
-    pp.a2 = __ldg(m.vals + pos);
+  if (q + kWideDepth < n) {
+    pp.a[kWideDepth - 1] = pp.an;
+    load_rec<false>(xr, pp.coln, 0, pp.rec[kWideDepth - 1]);
+  }
+  if (q + kWideDepth + 1 < n) {
+    const int64_t pos = pos0 + 32 * (int64_t)(q + kWideDepth + 1);
+    pp.coln = __ldg(m.cols + pos);
+    pp.an = __ldg(m.vals + pos);
   }
 }
 

@@ -275,10 +275,20 @@ __global__ void widen_kernel(const double* __restrict__ x, int64_t n, uint32_t* 
 }
 
 // Wide-x form, one row per thread (sliced-ELL copy) and one run per thread.
-// The real kernels keep two gathers in flight per thread (software
-// pipeline, run_body.cuh) and hold more registers: 6 resident blocks.
+// The real kernels keep a second gather in flight per thread (software
+// pipeline, run_body.cuh) and hold more registers.  Resident blocks, timed
+// over 5..7 blocks and pipeline depths 1..2 on the stencil and power-law
+// steps (depth 1 best throughout): the row kernel 6; the run kernel 6 for
+// DD and 5 for TD and QD (power-law QD 4.35 -> 4.07 ms).
+constexpr int kWideRowBlocks = 6;
+
+template <int L>
+constexpr int wide_run_blocks() {
+  return L == 2 ? 6 : 5;
+}
+
 template <int L, bool CPLX>
-__global__ void __launch_bounds__(kThreads, CPLX ? 3 : 6)
+__global__ void __launch_bounds__(kThreads, CPLX ? 3 : kWideRowBlocks)
     sell_wide_kernel(DevMat m, const int64_t* __restrict__ slice_ptr, const uint32_t* __restrict__ xw,
                      double* __restrict__ y, int64_t ys, const int* __restrict__ gate) {
   if (gate && *gate != 0) return;
@@ -288,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, CPLX ? 3 : 6)
 }
 
 template <int L, bool CPLX>
-__global__ void __launch_bounds__(kThreads, CPLX ? 3 : 6)
+__global__ void __launch_bounds__(kThreads, CPLX ? 3 : wide_run_blocks<L>())
     spmv_runs_wide_kernel(DevMat m, const uint32_t* __restrict__ xw, double* __restrict__ y, int64_t ys,
                           double* __restrict__ carry, int kc, const int* __restrict__ gate) {
   if (gate && *gate != 0) return;

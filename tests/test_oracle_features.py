@@ -96,8 +96,9 @@ def test_diagonal_matrix_and_exact_cg_step():
     bandwidth 0, row lengths constant); the largest |a_ii| is negative, so
     the upper Gershgorin bound (5) differs from max |a_ii| (7).  And binary64
     CG on diag(1, 3) with b = (1, 1): alpha = 2 / 4, r_1 = (1/2, -1/2),
-    ||r_1|| / ||b|| = 1/2, all exact in binary64; on 2^k I it stops after one step with r_1 = 0 exactly
-    (every later entry is the -300 of a zero norm)."""
+    ||r_1|| / ||b|| = 1/2, all exact in binary64; on 2^k I it stops after
+    one step with r_1 = 0 exactly (every later entry is the -300 of a zero
+    norm)."""
     d = np.array([-7.0, 1.0, 2.0, 5.0, 1.0])
     n = d.size
     A = _csr(workloads.COO(n, n, np.arange(n), np.arange(n), d[None, :]))

@@ -88,6 +88,36 @@ __device__ __forceinline__ void add_prod(Acc& acc, const mp<L>& a, const mp<L>& 
   }
 }
 
+// acc += u u (neg: -=) for an MP u: the same exact sum as add_prod(acc, u,
+// u, neg) with fewer products -- each symmetric pair u_i u_j + u_j u_i
+// (i != j, i + j < L - 1) is added once at twice the weight, which is exact,
+// and the FMA chain over i + j = L - 1 is add_prod's own.  QD: 4 exact
+// products instead of 6; TD: 2 instead of 3.
+template <class Acc, int L>
+__device__ __forceinline__ void add_prod_self(Acc& acc, const mp<L>& u, bool negate) {
+  if constexpr (L < 3) {
+    add_prod<Acc, L>(acc, u, u, negate);
+  } else if constexpr (L == 3) {
+    acc_add_prod(acc, u.v[0], u.v[0], negate);
+    double u0 = u.v[0], u1 = u.v[1];
+    asm volatile("" : "+d"(u0), "+d"(u1)::"memory");
+    fas_add_prod(acc, u0, u1, negate, 1);
+    const double c = __fma_rn(u.v[0], u.v[2], __fma_rn(u.v[1], u.v[1], __dmul_rn(u.v[2], u.v[0])));
+    acc_add(acc, c, negate);
+  } else {
+    const int ij[4][3] = {{0, 0, 0}, {0, 1, 1}, {0, 2, 1}, {1, 1, 0}};
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      double ui = u.v[ij[t][0]], uj = u.v[ij[t][1]];
+      asm volatile("" : "+d"(ui), "+d"(uj)::"memory");
+      fas_add_prod(acc, ui, uj, negate, ij[t][2]);
+    }
+    const double c =
+        __fma_rn(u.v[0], u.v[3], __fma_rn(u.v[1], u.v[2], __fma_rn(u.v[2], u.v[1], __dmul_rn(u.v[3], u.v[0]))));
+    acc_add(acc, c, negate);
+  }
+}
+
 // binary64 matrix value (M mode)
 template <class Acc, int L>
 __device__ __forceinline__ void add_prod_d(Acc& acc, double a, const mp<L>& x, bool negate) {

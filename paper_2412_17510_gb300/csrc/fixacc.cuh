@@ -329,15 +329,20 @@ __device__ __forceinline__ void fas_add(FixAccS<D, T>& a, double v, bool neg) {
 // (two binary64 instructions) and the two separate additions of its terms:
 // p + e of TwoProd is the same exact product.  Zero, subnormal and
 // non-finite operands take the binary64 path.
+// With twice = 1 the product is added at twice its weight (2 x y, exact: one
+// more in the exponent of its chunks).
 template <int D, int T>
-__device__ __forceinline__ void fas_add_prod(FixAccS<D, T>& a, double x, double y, bool neg) {
+__device__ __forceinline__ void fas_add_prod(FixAccS<D, T>& a, double x, double y, bool neg, int twice = 0) {
   const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
   const unsigned long long by = (unsigned long long)__double_as_longlong(y);
   const int ex = (int)((bx >> 52) & 0x7ff), ey = (int)((by >> 52) & 0x7ff);
   if ((unsigned)(ex - 1) >= 0x7feu || (unsigned)(ey - 1) >= 0x7feu) {
     const double p = __dmul_rn(x, y);
-    fas_add<D, T>(a, p, neg);
-    fas_add<D, T>(a, __fma_rn(x, y, -p), neg);
+    const double e = __fma_rn(x, y, -p);
+    for (int k = 0; k <= twice; k++) {
+      fas_add<D, T>(a, p, neg);
+      fas_add<D, T>(a, e, neg);
+    }
     return;
   }
   const bool negative = (((bx ^ by) >> 63) != 0) != neg;
@@ -345,7 +350,7 @@ __device__ __forceinline__ void fas_add_prod(FixAccS<D, T>& a, double x, double 
   const unsigned long long my = (by & 0xfffffffffffffULL) | (1ULL << 52);
   unsigned long long lo = mx * my;            // the product mx my < 2^106 as hi 2^64 + lo
   unsigned long long hi = __umul64hi(mx, my);
-  const int e0 = ex + ey - 2150;              // x y = mx my 2^e0
+  const int e0 = ex + ey - 2150 + twice;      // x y = mx my 2^e0 (times 2 with twice)
   int pos = e0 - a.base;
   if (pos > 32 * (D - 1) - 106) {             // top bit (at most e0 + 105) at or above digit D - 1
     a.base = fas_window<D, T>(a.dp, a.dn, a.base, e0 + 105);

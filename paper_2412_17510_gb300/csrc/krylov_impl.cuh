@@ -883,10 +883,15 @@ __device__ __forceinline__ cmp<L> x_sub(XAcc<L>& e, const cmp<L>& u, const cmp<L
 // and di is not touched
 template <int L, bool CPLX>
 __device__ __forceinline__ void x_dot(XAcc<L>& dr, XAcc<L>& di, const cmp<L>& u, const cmp<L>& v, bool self) {
+  if (self) {  // (u, u): the symmetric products once, doubled
+    add_prod_self<XAcc<L>, L>(dr, u.re, false);
+    if (CPLX) add_prod_self<XAcc<L>, L>(dr, u.im, false);
+    return;
+  }
   add_prod<XAcc<L>, L>(dr, u.re, v.re, false);
   if (CPLX) {
     add_prod<XAcc<L>, L>(dr, u.im, v.im, false);
-    if (!self) {
+    {
       add_prod<XAcc<L>, L>(di, u.re, v.im, false);
       add_prod<XAcc<L>, L>(di, u.im, v.re, true);
     }

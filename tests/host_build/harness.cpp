@@ -265,9 +265,36 @@ void wide_row_c(int n, const double* ar, const double* ai, const double* Xr, con
   mpk::fas_to_mp<L, D, 1>(si, out_im);
 }
 
+// sum over n MP values u_i (L components each) of u_i u_i, formed with
+// add_prod_self (self = 1) or add_prod(u, u) (self = 0), cut to L components
+template <int L>
+void self_sum(int self, int n, const double* U, double* out) {
+  constexpr int D = kD<L>;
+  unsigned long long dp[D], dn[D];
+  mpk::FixAccS<D, 1> acc;
+  acc.dp = dp;
+  acc.dn = dn;
+  mpk::fas_reset<D, 1>(acc);
+  for (int i = 0; i < n; i++) {
+    const mpk::mp<L> u = load_mp<L>(U + (int64_t)i * L);
+    if (self) mpk::add_prod_self<mpk::FixAccS<D, 1>, L>(acc, u, false);
+    else mpk::add_prod<mpk::FixAccS<D, 1>, L>(acc, u, u, false);
+  }
+  mpk::fas_to_mp<L, D, 1>(acc, out);
+}
+
 }  // namespace
 
 extern "C" {
+
+int host_self_sum(int L, int self, int n, const double* U, double* out) {
+  switch (L) {
+    case 2: self_sum<2>(self, n, U, out); return 0;
+    case 3: self_sum<3>(self, n, U, out); return 0;
+    case 4: self_sum<4>(self, n, U, out); return 0;
+    default: return -1;
+  }
+}
 
 int host_wide_rec(int L, const double* c, uint32_t* rec) {
   switch (L) {

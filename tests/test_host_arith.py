@@ -592,3 +592,36 @@ def test_wide_rows_equal_the_model(lib, L, cplx):
         compared += 1
         assert exact.bound_ratio(got[:, None], A, x) <= 1.0
     assert compared == 400
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_self_products_doubled_equal_the_plain_products(lib, L):
+    """Self inner products (u, u) take each symmetric pair u_i u_j + u_j u_i
+    once at twice the weight (add_prod_self): the same exact sum as
+    add_prod(u, u), the same FMA chain, so the same bits -- on single
+    elements over the exponent range (subnormal, zero and huge components
+    included) and on sums of elements of similar magnitude."""
+    lib.host_self_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+    rng = np.random.default_rng(500 + L)
+    cases = []
+    for i in range(3000):
+        u = workloads.full_limb_vector(1, L, rng=rng)[:, 0] * 2.0 ** int(rng.integers(-500, 500))
+        if i % 9 == 1:
+            u[1:] = -u[1:]
+        elif i % 9 == 2:
+            u[L - 1] = 0.0
+        elif i % 9 == 3:
+            u = workloads.full_limb_vector(1, L, rng=rng)[:, 0] * 2.0 ** -1040   # lower parts subnormal
+        elif i % 9 == 4:
+            u = workloads.full_limb_vector(1, L, rng=rng)[:, 0] * 2.0 ** 500
+        cases.append((1, u))
+    for i in range(300):
+        n = int(rng.integers(2, 20))
+        U = workloads.full_limb_vector(n, L, rng=rng).T * 2.0 ** int(rng.integers(-200, 200))
+        cases.append((n, U.reshape(-1)))
+    for n, U in cases:
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        a, b = np.zeros(L), np.zeros(L)
+        lib.host_self_sum(L, 1, n, U.ctypes.data_as(_dp), a.ctypes.data_as(_dp))
+        lib.host_self_sum(L, 0, n, U.ctypes.data_as(_dp), b.ctypes.data_as(_dp))
+        assert np.array_equal(a, b), (n, U, a, b)

@@ -165,7 +165,7 @@ class ClockSampler:
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("spmv.cu", "mp_arith.cuh", "run_body.cuh", "fixacc.cuh", "exact_prod.cuh", "api.cu"):
+    for f in ("spmv.cu", "mp_arith.cuh", "run_body.cuh", "fixacc.cuh", "exact_prod.cuh", "wide.cuh", "api.cu"):
         with open(os.path.join(ROOT, "paper_2412_17510_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

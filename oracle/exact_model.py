@@ -139,7 +139,8 @@ def axpy_model(L, alpha_re, alpha_im, u, v, cplx):
 # 2^-155, 2^-207).
 # ---------------------------------------------------------------------------
 WIDE_WORDS = {2: 4, 3: 5, 4: 7}
-WIDE_DIGITS = {2: 7, 3: 8, 4: 10}  # row accumulator digits of the wide form
+WIDE_DIGITS = {2: 8, 3: 9, 4: 11}  # row accumulator digits of the wide form
+WIDE_MARGIN = 32  # bits the window keeps above a product when it is placed or moved
 WSC = 4400  # wide-form terms are integers times 2^-4400
 
 
@@ -216,20 +217,21 @@ def wide_sum(L, prods):
     (sign, P, e0) of a row's products in the kernels' order.  Two
     non-negative digit arrays (positive and negative terms) of D digits with
     a common base: the first product's top bit (e0 + 20 + 32 W, the bound on
-    P) anchors the window in the last bit of digit D - 2; a product whose
-    top would reach digit D - 1 moves the window up by whole digits, each
-    array's value then floor-divided by 2^32 per digit (all digits cleared
-    for a move of D or more); a product's bits below the base are truncated.
-    Returns the sum, cut to L components."""
+    P), raised by the margin, anchors the window in the last bit of digit
+    D - 2; a product whose top would reach digit D - 1 moves the window up
+    by whole digits so that its top, raised by the margin, fits below digit
+    D - 1, each array's value then floor-divided by 2^32 per digit (all
+    digits cleared for a move of D or more); a product's bits below the base
+    are truncated.  Returns the sum, cut to L components."""
     W, D = WIDE_WORDS[L], WIDE_DIGITS[L]
     base = None
     vp = vn = 0
     for sg, P, e0 in prods:
         top = e0 + 20 + 32 * W
         if base is None:
-            base = top - (32 * (D - 1) - 1)
+            base = top + WIDE_MARGIN - (32 * (D - 1) - 1)
         elif e0 - base > 32 * (D - 1) - 21 - 32 * W:
-            sd = (top - base - (32 * (D - 1) - 1) + 31) >> 5
+            sd = (top + WIDE_MARGIN - base - (32 * (D - 1) - 1) + 31) >> 5
             if sd >= D:
                 vp = vn = 0
             else:

@@ -12,7 +12,8 @@
 // dropped), added to the row's exact sum as W + 2 aligned 32-bit chunks:
 // 6 / 7 / 9 digit updates per entry instead of 8 / 13 / 18, one decode of a,
 // one window test, and no binary64 instruction.  The row sum and its cut to
-// L components are those of fixacc.cuh.
+// L components are those of fixacc.cuh, in an accumulator one digit wider
+// (a margin above the products, so that the window rarely moves).
 //
 // Record of one column part (real or imaginary): 8 words of 32 bits, words
 // 0 .. W-1 the mantissa M (least significant first, top bit of word W-1 set
@@ -29,10 +30,16 @@ namespace mpk {
 
 template <int L>
 struct Wide {
-  static constexpr int W = L == 2 ? 4 : (L == 3 ? 5 : 7);  // mantissa words
-  static constexpr int DX = W + 2;                         // digits of the record's construction
-  static constexpr int D = L == 2 ? 7 : (L == 3 ? 8 : 10); // digits of the row accumulator
+  static constexpr int W = L == 2 ? 4 : (L == 3 ? 5 : 7);   // mantissa words
+  static constexpr int DX = W + 2;                          // digits of the record's construction
+  static constexpr int D = L == 2 ? 8 : (L == 3 ? 9 : 11);  // digits of the row accumulator
 };
+
+// Bits the row window keeps above a product when it is placed (the row's
+// first product) or moved: later products up to 2^32 larger than the one
+// that placed it do not move it again.  The extra digit of Wide<L>::D holds
+// this margin, so the window's lower end is where it would be without it.
+constexpr int kWideMargin = 32;
 
 constexpr int kWideRecWords = 8;
 
@@ -172,7 +179,7 @@ __device__ __forceinline__ void fas_add_wide(FixAccS<D, T>& acc, double a, const
   int pos = e0 - acc.base;
   // P has at most 53 + 32 W - 32 bits: its top bit lies at most at pos + 20 + 32 W
   if (pos > 32 * (D - 1) - 21 - 32 * W) {
-    acc.base = fas_window<D, T>(acc.dp, acc.dn, acc.base, e0 + 20 + 32 * W);
+    acc.base = fas_window<D, T>(acc.dp, acc.dn, acc.base, e0 + 20 + 32 * W + kWideMargin);
     pos = e0 - acc.base;
   }
   unsigned long long* p = negative ? acc.dn : acc.dp;

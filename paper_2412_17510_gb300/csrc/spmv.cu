@@ -277,14 +277,15 @@ __global__ void widen_kernel(const double* __restrict__ x, int64_t n, uint32_t* 
 // Wide-x form, one row per thread (sliced-ELL copy) and one run per thread.
 // The real kernels keep a second gather in flight per thread (software
 // pipeline, run_body.cuh) and hold more registers.  Resident blocks, timed
-// over 5..7 blocks and pipeline depths 1..2 on the stencil and power-law
-// steps (depth 1 best throughout): the row kernel 6; the run kernel 6 for
-// DD and 5 for TD and QD (power-law QD 4.35 -> 4.07 ms).
+// over 4..7 blocks and pipeline depths 1..2 on the stencil and power-law
+// steps (depth 1 best throughout): the row kernel 6; the run kernel 5 for
+// DD and TD and 4 for QD (with 6 the DD kernel spills: power-law DD
+// 2.92 -> 2.59 ms at 5).
 constexpr int kWideRowBlocks = 6;
 
 template <int L>
 constexpr int wide_run_blocks() {
-  return L == 2 ? 6 : 5;
+  return L == 4 ? 4 : 5;
 }
 
 template <int L, bool CPLX>

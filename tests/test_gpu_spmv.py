@@ -230,6 +230,39 @@ def test_host_buffer_entry_point():
         mps.mpspmv_destroy(h)
 
 
+def test_async_host_buffer_entry_point_on_two_streams():
+    """mpspmv_spmv_host_async: products of three handles (paper order, exact
+    on binary64 values, complex) enqueued on two streams with pinned host
+    buffers, twice in a row; after the streams complete, every y equals the
+    device-buffer product of the same handle."""
+    cases = []
+    coo = workloads.laplacian_2d(40)
+    cases.append((coo, 3, 0, coo.val))
+    coo2 = workloads.power_law(2000, seed=4)
+    cases.append((coo2, 4, mps.MPSPMV_EXACT_ACC, coo2.val))
+    coo3 = workloads.complex_sym_banded(900, 5, 0.5, seed=2)
+    cases.append((coo3, 2, mps.MPSPMV_COMPLEX, coo3.val))
+    hs, xs, ys = [], [], []
+    try:
+        for c, L, fl, v in cases:
+            h = mps.mpspmv_create_csr(c.nrows, c.ncols, c.row, c.col, v, L, fl, val_limbs=1)
+            P = mps.mpspmv_get_info(h)["planes"]
+            hs.append((h, P, c))
+            xs.append(torch.from_numpy(workloads.full_limb_vector(c.ncols, L, seed=12, cplx=c.cplx)).pin_memory())
+            ys.append(torch.full((P, c.nrows), float("nan"), dtype=torch.float64).pin_memory())
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        for _ in range(2):
+            for i, ((h, P, c), xh, yh) in enumerate(zip(hs, xs, ys)):
+                mps.mpspmv_spmv_host_async(h, xh, yh, streams[i % 2])
+        for s in streams:
+            s.synchronize()
+        for (h, P, c), xh, yh in zip(hs, xs, ys):
+            assert np.array_equal(yh.numpy(), gpu_spmv(h, xh.numpy(), P, c.nrows))
+    finally:
+        for h, _, _ in hs:
+            mps.mpspmv_destroy(h)
+
+
 def test_invalid_arguments():
     with pytest.raises(mps.MpspmvError) as e:
         mps.mpspmv_create_csr(5, 5, [0, 5], [0, 0], np.ones((1, 2)), 2)

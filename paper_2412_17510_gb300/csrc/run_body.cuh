@@ -395,13 +395,16 @@ __device__ __forceinline__ void process_row_wide(const DevMat& m, int64_t base, 
     }
   }
   mp<L> vr, vi = mp_zero<L>();
-  fas_to_mp<L, D, T>(sr, vr.v);
-  if (CPLX) fas_to_mp<L, D, T>(si, vi.v);
+  fas_to_mp_inline<L, D, T>(sr, vr.v);
+  if (CPLX) fas_to_mp_inline<L, D, T>(si, vi.v);
   store_mp<L, CPLX>(y, ys, r, vr, vi);
 }
 
 // One run per thread, wide-x form: the run structure, carries and empty-row
-// handling of process_run_exact (single right-hand side).
+// handling of process_run_exact (single right-hand side).  The row flushes
+// are inline here (fas_to_mp_inline): the wide kernels hold fewer registers
+// per entry than the decomposed ones, and the call cost more than it saved
+// (power-law QD 3.90 -> 3.67 ms).
 template <int L, bool CPLX, int T>
 __device__ __forceinline__ void process_run_wide(const DevMat& m, int64_t c, const uint32_t* __restrict__ xr,
                                                  double* __restrict__ y, int64_t ys, double* __restrict__ carry,
@@ -445,8 +448,8 @@ __device__ __forceinline__ void process_run_wide(const DevMat& m, int64_t c, con
     const int64_t kk = k0 + j + 1;
     if (kk == rend) {
       mp<L> vr, vi = z;
-      fas_to_mp_to<L, D, T>(sr, vr.v);
-      if (CPLX) fas_to_mp_to<L, D, T>(si, vi.v);
+      fas_to_mp_inline<L, D, T>(sr, vr.v);
+      if (CPLX) fas_to_mp_inline<L, D, T>(si, vi.v);
       if (row == first_row && first_partial) {
 #pragma unroll
         for (int p = 0; p < P; p++) carry[((int64_t)p * m.nchunks + c) * kc] = p < L ? vr.v[p % L] : vi.v[p % L];
@@ -466,8 +469,8 @@ __device__ __forceinline__ void process_run_wide(const DevMat& m, int64_t c, con
   }
   if (have) {
     mp<L> vr, vi = z;
-    fas_to_mp_to<L, D, T>(sr, vr.v);
-    if (CPLX) fas_to_mp_to<L, D, T>(si, vi.v);
+    fas_to_mp_inline<L, D, T>(sr, vr.v);
+    if (CPLX) fas_to_mp_inline<L, D, T>(si, vi.v);
     const int w = (row == first_row && first_partial) ? 0 : 1;
 #pragma unroll
     for (int p = 0; p < P; p++)

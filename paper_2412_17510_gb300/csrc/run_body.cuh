@@ -301,69 +301,114 @@ __device__ __forceinline__ void load_rec(const uint32_t* __restrict__ xr, int64_
 // instead of one.
 constexpr int kWideDepth = 1;
 
+// V = 1 (real) or 2 (complex: the real part's record and value, then the
+// imaginary part's)
+template <int V>
 struct WidePipe {
-  uint32_t rec[kWideDepth][kWideRecWords];  // records of the next entries
-  double a[kWideDepth];                     // their values
-  int64_t coln;                             // column of the entry after them
-  double an;                                // its value
+  uint32_t rec[kWideDepth][V][kWideRecWords];  // records of the next entries
+  double a[kWideDepth][V];                     // their values
+  int64_t coln;                                // column of the entry after them
+  double an[V];                                // its value
 };
 
+template <int V>
+__device__ __forceinline__ void wide_load_vals(const DevMat& m, int64_t pos, double* a) {
+  a[0] = __ldg(m.vals + pos);
+  if (V == 2) a[1] = __ldg(m.vals + m.tlen + pos);
+}
+
+template <int V>
+__device__ __forceinline__ void wide_load_recs(const uint32_t* __restrict__ xr, int64_t col,
+                                               uint32_t (&rec)[V][kWideRecWords]) {
+#pragma unroll
+  for (int p = 0; p < V; p++) load_rec<V == 2>(xr, col, p, rec[p]);
+}
+
+template <int V>
 __device__ __forceinline__ void wide_pipe_start(const DevMat& m, int64_t pos0, int n, const uint32_t* __restrict__ xr,
-                                                WidePipe& pp) {
+                                                WidePipe<V>& pp) {
 #pragma unroll
   for (int i = 0; i < kWideDepth; i++) {
     if (i < n) {
       const int64_t pos = pos0 + 32 * (int64_t)i;
-      pp.a[i] = __ldg(m.vals + pos);
-      load_rec<false>(xr, __ldg(m.cols + pos), 0, pp.rec[i]);
+      wide_load_vals<V>(m, pos, pp.a[i]);
+      wide_load_recs<V>(xr, __ldg(m.cols + pos), pp.rec[i]);
     }
   }
   if (kWideDepth < n) {
     const int64_t pos = pos0 + 32 * (int64_t)kWideDepth;
     pp.coln = __ldg(m.cols + pos);
-    pp.an = __ldg(m.vals + pos);
+    wide_load_vals<V>(m, pos, pp.an);
   }
 }
 
+template <int V>
 __device__ __forceinline__ void wide_pipe_step(const DevMat& m, int64_t pos0, int q, int n,
-                                               const uint32_t* __restrict__ xr, WidePipe& pp, double& a,
-                                               uint32_t* rec) {
-  a = pp.a[0];
+                                               const uint32_t* __restrict__ xr, WidePipe<V>& pp, double (&a)[V],
+                                               uint32_t (&rec)[V][kWideRecWords]) {
 #pragma unroll
-  for (int w = 0; w < kWideRecWords; w++) rec[w] = pp.rec[0][w];
+  for (int p = 0; p < V; p++) {
+    a[p] = pp.a[0][p];
 #pragma unroll
-  for (int i = 0; i + 1 < kWideDepth; i++) {
-    pp.a[i] = pp.a[i + 1];
-#pragma unroll
-    for (int w = 0; w < kWideRecWords; w++) pp.rec[i][w] = pp.rec[i + 1][w];
+    for (int w = 0; w < kWideRecWords; w++) rec[p][w] = pp.rec[0][p][w];
   }
+#pragma unroll
+  for (int i = 0; i + 1 < kWideDepth; i++)
+#pragma unroll
+    for (int p = 0; p < V; p++) {
+      pp.a[i][p] = pp.a[i + 1][p];
+#pragma unroll
+      for (int w = 0; w < kWideRecWords; w++) pp.rec[i][p][w] = pp.rec[i + 1][p][w];
+    }
   if (q + kWideDepth < n) {
-    pp.a[kWideDepth - 1] = pp.an;
-    load_rec<false>(xr, pp.coln, 0, pp.rec[kWideDepth - 1]);
+#pragma unroll
+    for (int p = 0; p < V; p++) pp.a[kWideDepth - 1][p] = pp.an[p];
+    wide_load_recs<V>(xr, pp.coln, pp.rec[kWideDepth - 1]);
   }
   if (q + kWideDepth + 1 < n) {
     const int64_t pos = pos0 + 32 * (int64_t)(q + kWideDepth + 1);
     pp.coln = __ldg(m.cols + pos);
-    pp.an = __ldg(m.vals + pos);
+    wide_load_vals<V>(m, pos, pp.an);
   }
 }
 
+// One entry's products into the row sums (complex in the order re += a_re
+// X_re, im += a_im X_re, re -= a_im X_im, im += a_re X_im).
 template <int L, bool CPLX, int D, int T>
-__device__ __forceinline__ void wide_entry(const DevMat& m, int64_t pos, const uint32_t* __restrict__ xr,
-                                           FixAccS<D, T>& sr, FixAccS<D, T>& si) {
-  const int64_t col = __ldg(m.cols + pos);
-  const double ar = __ldg(m.vals + pos);
-  uint32_t rec[kWideRecWords];
-  load_rec<CPLX>(xr, col, 0, rec);
-  fas_add_wide<L, D, T>(sr, ar, rec, false);
-  if (CPLX) {
-    const double ai = __ldg(m.vals + m.tlen + pos);
-    fas_add_wide<L, D, T>(si, ai, rec, false);   // a_im X_re
-    load_rec<CPLX>(xr, col, 1, rec);
-    fas_add_wide<L, D, T>(sr, ai, rec, true);    // - a_im X_im
-    fas_add_wide<L, D, T>(si, ar, rec, false);   // a_re X_im
+__device__ __forceinline__ void wide_sum_entry(const double (&a)[CPLX ? 2 : 1],
+                                               const uint32_t (&rec)[CPLX ? 2 : 1][kWideRecWords],
+                                               FixAccS<D, T>& sr, FixAccS<D, T>& si) {
+  fas_add_wide<L, D, T>(sr, a[0], rec[0], false);
+  if constexpr (CPLX) {
+    fas_add_wide<L, D, T>(si, a[1], rec[0], false);
+    fas_add_wide<L, D, T>(sr, a[1], rec[1], true);
+    fas_add_wide<L, D, T>(si, a[0], rec[1], false);
   }
 }
+
+// One complex entry loaded in the step that sums it (the imaginary part's
+// record after the real part's two products).  Complex QD takes this form:
+// with two records in flight its registers cost more than the pipeline
+// saved (A/B on the complex band: 10.8 against 9.8 Gnnz/s), while complex DD
+// and TD gain from the pipeline (DD 18.6 -> 21.9).
+template <int L, int D, int T>
+__device__ __forceinline__ void wide_entry_cplx(const DevMat& m, int64_t pos, const uint32_t* __restrict__ xr,
+                                                FixAccS<D, T>& sr, FixAccS<D, T>& si) {
+  const int64_t col = __ldg(m.cols + pos);
+  const double ar = __ldg(m.vals + pos), ai = __ldg(m.vals + m.tlen + pos);
+  uint32_t rec[kWideRecWords];
+  load_rec<true>(xr, col, 0, rec);
+  fas_add_wide<L, D, T>(sr, ar, rec, false);   // a_re X_re
+  fas_add_wide<L, D, T>(si, ai, rec, false);   // a_im X_re
+  load_rec<true>(xr, col, 1, rec);
+  fas_add_wide<L, D, T>(sr, ai, rec, true);    // - a_im X_im
+  fas_add_wide<L, D, T>(si, ar, rec, false);   // a_re X_im
+}
+
+template <int L, bool CPLX>
+struct WidePipelined {
+  static constexpr bool value = !(CPLX && L == 4);
+};
 
 // One row per thread from the sliced-ELL copy, wide-x form.
 template <int L, bool CPLX, int T>
@@ -380,19 +425,20 @@ __device__ __forceinline__ void process_row_wide(const DevMat& m, int64_t base, 
   if (CPLX) fas_reset<D, T>(si);
   const int64_t len = __ldg(m.indptr + r + 1) - __ldg(m.indptr + r);
   const int64_t slot0 = base + (r & 31);
-  if constexpr (CPLX) {
-#pragma unroll 1
-    for (int64_t q = 0; q < len; q++) wide_entry<L, CPLX, D, T>(m, slot0 + 32 * q, xr, sr, si);
-  } else {
-    WidePipe pp;
-    wide_pipe_start(m, slot0, (int)len, xr, pp);
+  if constexpr (WidePipelined<L, CPLX>::value) {
+    constexpr int V = CPLX ? 2 : 1;
+    WidePipe<V> pp;
+    wide_pipe_start<V>(m, slot0, (int)len, xr, pp);
 #pragma unroll 1
     for (int q = 0; q < (int)len; q++) {
-      double a;
-      uint32_t rec[kWideRecWords];
-      wide_pipe_step(m, slot0, q, (int)len, xr, pp, a, rec);
-      fas_add_wide<L, D, T>(sr, a, rec, false);
+      double a[V];
+      uint32_t rec[V][kWideRecWords];
+      wide_pipe_step<V>(m, slot0, q, (int)len, xr, pp, a, rec);
+      wide_sum_entry<L, CPLX, D, T>(a, rec, sr, si);
     }
+  } else {
+#pragma unroll 1
+    for (int64_t q = 0; q < len; q++) wide_entry_cplx<L, D, T>(m, slot0 + 32 * q, xr, sr, si);
   }
   mp<L> vr, vi = mp_zero<L>();
   fas_to_mp_inline<L, D, T>(sr, vr.v);
@@ -432,17 +478,18 @@ __device__ __forceinline__ void process_run_wide(const DevMat& m, int64_t c, con
   bool have = false;
   const int n = (int)(k1 - k0);
   const int64_t chunk_base = tile_pos(c, 0, m.K);
-  WidePipe pp;
-  if (!CPLX) wide_pipe_start(m, chunk_base, n, xr, pp);
+  constexpr int V = CPLX ? 2 : 1;
+  WidePipe<V> pp;
+  if constexpr (WidePipelined<L, CPLX>::value) wide_pipe_start<V>(m, chunk_base, n, xr, pp);
 #pragma unroll 1
   for (int j = 0; j < n; j++) {
-    if constexpr (CPLX) {
-      wide_entry<L, CPLX, D, T>(m, chunk_base + (int64_t)j * 32, xr, sr, si);
+    if constexpr (WidePipelined<L, CPLX>::value) {
+      double a[V];
+      uint32_t rec[V][kWideRecWords];
+      wide_pipe_step<V>(m, chunk_base, j, n, xr, pp, a, rec);
+      wide_sum_entry<L, CPLX, D, T>(a, rec, sr, si);
     } else {
-      double a;
-      uint32_t rec[kWideRecWords];
-      wide_pipe_step(m, chunk_base, j, n, xr, pp, a, rec);
-      fas_add_wide<L, D, T>(sr, a, rec, false);
+      wide_entry_cplx<L, D, T>(m, chunk_base + (int64_t)j * 32, xr, sr, si);
     }
     have = true;
     const int64_t kk = k0 + j + 1;

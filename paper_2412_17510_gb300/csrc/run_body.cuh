@@ -294,21 +294,30 @@ __device__ __forceinline__ void load_rec(const uint32_t* __restrict__ xr, int64_
   rec[4] = u1.x; rec[5] = u1.y; rec[6] = u1.z; rec[7] = u1.w;
 }
 
-// Software pipeline of a real entry stream (entry q at pos0 + 32 q): while
-// entry q is summed, the records of entries q + 1 .. q + kWideDepth are
-// already being gathered and the column and value of the entry after them
-// loaded, so each thread keeps kWideDepth dependent gathers in flight
-// instead of one.
-constexpr int kWideDepth = 1;
+// Software pipeline of an entry stream (entry q at pos0 + 32 q).  Before
+// entry q is summed the pipe holds the records and values of entries
+// q .. q + kWideRecAhead - 1 (their gathers issued) and the columns and values
+// of entries q + kWideRecAhead .. q + kWideColAhead - 1 (loads issued).  Each
+// step takes entry q, issues the gather of entry q + kWideRecAhead from the
+// column that arrived and loads the column and value of entry
+// q + kWideColAhead.  Depths chosen by timing the benchmark's matrices: one
+// record and one column ahead is fastest (columns 2 or 3 entries ahead, or
+// two records ahead, cost registers and time; power-law TD 2.85 -> 3.07 ms
+// with columns 2 ahead).  Holding the column as 32 bits instead of 64 took
+// power-law QD from 3.67 to 3.31 ms and the stencil from 0.638 to 0.574 ms.
+constexpr int kWideRecAhead = 1;
+constexpr int kWideColAhead = 2;
+constexpr int kWideColSlots = kWideColAhead - kWideRecAhead;
+static_assert(kWideRecAhead >= 1 && kWideColSlots >= 1, "pipeline depths");
 
 // V = 1 (real) or 2 (complex: the real part's record and value, then the
 // imaginary part's)
 template <int V>
 struct WidePipe {
-  uint32_t rec[kWideDepth][V][kWideRecWords];  // records of the next entries
-  double a[kWideDepth][V];                     // their values
-  int64_t coln;                                // column of the entry after them
-  double an[V];                                // its value
+  uint32_t rec[kWideRecAhead][V][kWideRecWords];  // gathered records
+  double a[kWideRecAhead][V];                     // their values
+  int32_t col[kWideColSlots];                     // columns of the entries after them
+  double av[kWideColSlots][V];                    // their values
 };
 
 template <int V>
@@ -328,17 +337,20 @@ template <int V>
 __device__ __forceinline__ void wide_pipe_start(const DevMat& m, int64_t pos0, int n, const uint32_t* __restrict__ xr,
                                                 WidePipe<V>& pp) {
 #pragma unroll
-  for (int i = 0; i < kWideDepth; i++) {
+  for (int i = 0; i < kWideRecAhead; i++) {
     if (i < n) {
       const int64_t pos = pos0 + 32 * (int64_t)i;
       wide_load_vals<V>(m, pos, pp.a[i]);
       wide_load_recs<V>(xr, __ldg(m.cols + pos), pp.rec[i]);
     }
   }
-  if (kWideDepth < n) {
-    const int64_t pos = pos0 + 32 * (int64_t)kWideDepth;
-    pp.coln = __ldg(m.cols + pos);
-    wide_load_vals<V>(m, pos, pp.an);
+#pragma unroll
+  for (int i = 0; i < kWideColSlots; i++) {
+    if (kWideRecAhead + i < n) {
+      const int64_t pos = pos0 + 32 * (int64_t)(kWideRecAhead + i);
+      pp.col[i] = __ldg(m.cols + pos);
+      wide_load_vals<V>(m, pos, pp.av[i]);
+    }
   }
 }
 
@@ -353,22 +365,28 @@ __device__ __forceinline__ void wide_pipe_step(const DevMat& m, int64_t pos0, in
     for (int w = 0; w < kWideRecWords; w++) rec[p][w] = pp.rec[0][p][w];
   }
 #pragma unroll
-  for (int i = 0; i + 1 < kWideDepth; i++)
+  for (int i = 0; i + 1 < kWideRecAhead; i++)
 #pragma unroll
     for (int p = 0; p < V; p++) {
       pp.a[i][p] = pp.a[i + 1][p];
 #pragma unroll
       for (int w = 0; w < kWideRecWords; w++) pp.rec[i][p][w] = pp.rec[i + 1][p][w];
     }
-  if (q + kWideDepth < n) {
+  if (q + kWideRecAhead < n) {
 #pragma unroll
-    for (int p = 0; p < V; p++) pp.a[kWideDepth - 1][p] = pp.an[p];
-    wide_load_recs<V>(xr, pp.coln, pp.rec[kWideDepth - 1]);
+    for (int p = 0; p < V; p++) pp.a[kWideRecAhead - 1][p] = pp.av[0][p];
+    wide_load_recs<V>(xr, pp.col[0], pp.rec[kWideRecAhead - 1]);
   }
-  if (q + kWideDepth + 1 < n) {
-    const int64_t pos = pos0 + 32 * (int64_t)(q + kWideDepth + 1);
-    pp.coln = __ldg(m.cols + pos);
-    wide_load_vals<V>(m, pos, pp.an);
+#pragma unroll
+  for (int i = 0; i + 1 < kWideColSlots; i++) {
+    pp.col[i] = pp.col[i + 1];
+#pragma unroll
+    for (int p = 0; p < V; p++) pp.av[i][p] = pp.av[i + 1][p];
+  }
+  if (q + kWideColAhead < n) {
+    const int64_t pos = pos0 + 32 * (int64_t)(q + kWideColAhead);
+    pp.col[kWideColSlots - 1] = __ldg(m.cols + pos);
+    wide_load_vals<V>(m, pos, pp.av[kWideColSlots - 1]);
   }
 }
 

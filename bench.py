@@ -891,10 +891,11 @@ def main():
         i = v["info"]
         if v["arith"] != "exact":
             return 1 + (i["nsplit_rows"] > i["nlong_rows"]) + (i["nlong_rows"] > 0)
-        inter = 1 if v["L"] > 1 else 0  # interleaved copy of x
+        inter = 1 if v["L"] > 1 else 0  # x records (wide-x form) or interleaved copy of x
         if i["sell_slots"] > 0:
             return inter + 1            # one row per thread
-        return inter + 1 + (i["nsplit_rows"] > i["nlong_rows"]) + (i["nlong_rows"] > 0)
+        finish = 1 if v["L"] > 1 else 0  # finishing pass of the staged rows (real wide-x form)
+        return inter + 1 + finish + (i["nsplit_rows"] > i["nlong_rows"]) + (i["nlong_rows"] > 0)
 
     launches_per_step = R * sum(launches_of(v) for v in variants)
 

@@ -41,6 +41,7 @@ void free_handle(mpspmv_mat* h) {
   cudaFree(h->d_carry);
   cudaFree(h->d_xint);
   cudaFree(h->d_xwide);
+  cudaFree(h->d_rowdig);
   cudaFree(h->d_slice_ptr);
   cudaFree(h->d_sell_cols);
   cudaFree(h->d_sell_vals);
@@ -313,6 +314,8 @@ int create_impl(mpspmv_h* out, int64_t nrows, int64_t ncols, int64_t nnz_in, con
       }
       TRY(mps_build_tiles(h, d_vin, nin, (mixed || h->dstore) ? 1 : val_limbs, d_runs, d_col, s));
       if (h->exact) TRY(mps_build_sell(h, s));
+      if (h->d_xwide && !h->cplx && h->sell_len == 0 && nrows > 0)
+        TRY(dev_alloc(h, &h->d_rowdig, nrows * (int64_t)kRowDigWords));
       if (cudaStreamSynchronize(s) != cudaSuccess) {
         st = MPSPMV_ECUDA;
         goto fail;

@@ -42,6 +42,12 @@ struct DevMat {
 // Rows whose entries span more than this many chunks are combined by a warp.
 constexpr int kLongSpan = 32;
 
+// Words per row of the finished-row buffer of real wide-x products over runs:
+// the row accumulator's digit differences (at most 11 digits, QD) and one
+// word with its window base (low half) and flush flags (high half); 96
+// bytes, three DRAM sectors.
+constexpr int kRowDigWords = 12;
+
 struct mpspmv_mat {
   int device;
   int L, P, Pv;  // components, vector planes, stored value planes
@@ -62,6 +68,8 @@ struct mpspmv_mat {
   int carry_k = 0;                // right-hand sides the carry buffer holds
   double* d_xint = nullptr;       // exact handles: x with the P components of a column adjacent
   uint32_t* d_xwide = nullptr;    // exact handles with one value plane: the wide-x records of x (wide.cuh)
+  int64_t* d_rowdig = nullptr;    // real wide-x products over runs: per row, the finished row's digits
+                                  // (kRowDigWords words) for the finishing pass
   // Exact handles with short, evenly sized rows: a sliced-ELL copy for
   // single-vector products (slices of 32 rows, entry q of row r at
   // slice_ptr[r / 32] + 32 q + r % 32), one thread per row.

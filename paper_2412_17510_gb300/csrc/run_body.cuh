@@ -464,6 +464,22 @@ __device__ __forceinline__ void process_row_wide(const DevMat& m, int64_t base, 
   store_mp<L, CPLX>(y, ys, r, vr, vi);
 }
 
+// A finished row of a real wide-x run, staged for the finishing pass: the
+// accumulator's D signed digit differences dp_j - dn_j (each digit is below
+// 2^63, so the difference fits) and one word with the window base and the
+// flags the flush takes.  The finishing pass runs the flush on these digits,
+// so the components are those of the inline flush; the run kernel's part is
+// about a quarter of the flush's instructions, and the divergent lanes (only
+// those whose row ends at this entry) wait that much less.
+template <int D, int T>
+__device__ __forceinline__ void fas_stage(const FixAccS<D, T>& a, int64_t* __restrict__ out) {
+  static_assert(D + 1 <= kRowDigWords, "row buffer words");
+#pragma unroll
+  for (int j = 0; j < D; j++) out[j] = (long long)a.dp[j * T] - (long long)a.dn[j * T];
+  const int flags = (a.base != kNotLive ? 1 : 0) | (a.bad ? 2 : 0);
+  out[D] = (int64_t)(uint32_t)a.base | ((int64_t)flags << 32);
+}
+
 // One run per thread, wide-x form: the run structure, carries and empty-row
 // handling of process_run_exact (single right-hand side).  The row flushes
 // are inline here (fas_to_mp_inline): the wide kernels hold fewer registers
@@ -472,7 +488,7 @@ __device__ __forceinline__ void process_row_wide(const DevMat& m, int64_t base, 
 template <int L, bool CPLX, int T>
 __device__ __forceinline__ void process_run_wide(const DevMat& m, int64_t c, const uint32_t* __restrict__ xr,
                                                  double* __restrict__ y, int64_t ys, double* __restrict__ carry,
-                                                 int kc) {
+                                                 int kc, int64_t* __restrict__ rowdig) {
   constexpr int P = CPLX ? 2 * L : L;
   constexpr int D = Wide<L>::D;
   __shared__ unsigned long long s_digits[(CPLX ? 4 : 2) * D * T];
@@ -512,14 +528,20 @@ __device__ __forceinline__ void process_run_wide(const DevMat& m, int64_t c, con
     have = true;
     const int64_t kk = k0 + j + 1;
     if (kk == rend) {
-      mp<L> vr, vi = z;
-      fas_to_mp_inline<L, D, T>(sr, vr.v);
-      if (CPLX) fas_to_mp_inline<L, D, T>(si, vi.v);
-      if (row == first_row && first_partial) {
+      if constexpr (CPLX) {
+        mp<L> vr, vi;
+        fas_to_mp_inline<L, D, T>(sr, vr.v);
+        fas_to_mp_inline<L, D, T>(si, vi.v);
+        if (row == first_row && first_partial) {
 #pragma unroll
-        for (int p = 0; p < P; p++) carry[((int64_t)p * m.nchunks + c) * kc] = p < L ? vr.v[p % L] : vi.v[p % L];
+          for (int p = 0; p < P; p++) carry[((int64_t)p * m.nchunks + c) * kc] = p < L ? vr.v[p % L] : vi.v[p % L];
+        } else {
+          store_mp<L, CPLX>(y, ys, row, vr, vi);
+        }
       } else {
-        store_mp<L, CPLX>(y, ys, row, vr, vi);
+        // the finishing pass writes y, or for a row begun in an earlier run
+        // this run's partial into the carry buffer
+        fas_stage<D, T>(sr, rowdig + row * kRowDigWords);
       }
       fas_reset<D, T>(sr);
       if (CPLX) fas_reset<D, T>(si);

@@ -277,15 +277,17 @@ __global__ void widen_kernel(const double* __restrict__ x, int64_t n, uint32_t* 
 // Wide-x form, one row per thread (sliced-ELL copy) and one run per thread.
 // The real kernels keep a second gather in flight per thread (software
 // pipeline, run_body.cuh) and hold more registers.  Resident blocks, timed
-// over 4..7 blocks and pipeline depths 1..2 on the stencil and power-law
-// steps (depth 1 best throughout): the row kernel 6; the run kernel 5 for
-// DD and TD and 4 for QD (with 6 the DD kernel spills: power-law DD
-// 2.92 -> 2.59 ms at 5).
+// on the stencil and power-law steps: the row kernel 6; the real run kernel,
+// whose loop stages finished rows instead of flushing them (82 / 88 / 96
+// registers for DD / TD / QD), 6 for DD (power-law DD 2.21 -> 2.15 ms
+// against 5; at 7 it spills), 5 for TD and 4 for QD.  The QD kernel then
+// takes 96 registers and runs 5 blocks per SM all the same; a bound of 5
+// compiles to a slightly slower kernel (2.89 against 2.87 ms).
 constexpr int kWideRowBlocks = 6;
 
 template <int L>
 constexpr int wide_run_blocks() {
-  return L == 4 ? 4 : 5;
+  return L == 2 ? 6 : (L == 3 ? 5 : 4);
 }
 
 template <int L, bool CPLX>
@@ -301,11 +303,52 @@ __global__ void __launch_bounds__(kThreads, CPLX ? 3 : kWideRowBlocks)
 template <int L, bool CPLX>
 __global__ void __launch_bounds__(kThreads, CPLX ? 3 : wide_run_blocks<L>())
     spmv_runs_wide_kernel(DevMat m, const uint32_t* __restrict__ xw, double* __restrict__ y, int64_t ys,
-                          double* __restrict__ carry, int kc, const int* __restrict__ gate) {
+                          double* __restrict__ carry, int kc, int64_t* __restrict__ rowdig,
+                          const int* __restrict__ gate) {
   if (gate && *gate != 0) return;
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= m.nchunks) return;
-  process_run_wide<L, CPLX, kThreads>(m, c, xw, y, ys, carry, kc);
+  process_run_wide<L, CPLX, kThreads>(m, c, xw, y, ys, carry, kc, rowdig);
+}
+
+// The finishing pass of real wide-x products over runs, one row per thread.
+// The run kernel staged (fas_stage) the sum of every non-empty row over the
+// run that holds its last entry; it is flushed here, with the flush
+// arithmetic of the run kernels.  A row whose entries all lie in that run
+// goes to y; a row begun in an earlier run is that run's first partial and
+// goes to the carry buffer (slot 0 of the run), which the combine kernels
+// read after this pass.  Empty rows are written by the run kernel.
+template <int L>
+__global__ void __launch_bounds__(kThreads) rowdig_finish_kernel(DevMat m, const int64_t* __restrict__ rowdig,
+                                                                 double* __restrict__ y, int64_t ys,
+                                                                 double* __restrict__ carry, int kc,
+                                                                 const int* __restrict__ gate) {
+  if (gate && *gate != 0) return;
+  const int64_t r = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  if (r >= m.nrows) return;
+  const int64_t k0 = __ldg(m.indptr + r), k1 = __ldg(m.indptr + r + 1);
+  if (k1 == k0) return;
+  const int64_t c1 = (k1 - 1) / m.K;
+  constexpr int D = Wide<L>::D;
+  __shared__ unsigned long long s_digits[2 * D * kThreads];
+  unsigned long long* dp = s_digits + threadIdx.x;
+  unsigned long long* dn = s_digits + D * kThreads + threadIdx.x;
+  const int64_t* q = rowdig + r * kRowDigWords;
+#pragma unroll
+  for (int j = 0; j < D; j++) {
+    dp[j * kThreads] = (unsigned long long)__ldg(q + j);  // dp - dn is the staged difference
+    dn[j * kThreads] = 0ull;
+  }
+  const int64_t meta = __ldg(q + D);
+  double v[L];
+  fas_flush_body<L, D, kThreads>(dp, dn, (int)(uint32_t)meta, (int)(meta >> 32), v);
+  if (k0 / m.K == c1) {
+#pragma unroll
+    for (int l = 0; l < L; l++) y[(int64_t)l * ys + r] = v[l];
+  } else {
+#pragma unroll
+    for (int l = 0; l < L; l++) carry[((int64_t)l * m.nchunks + c1) * kc] = v[l];
+  }
 }
 
 // y = 0 (single right-hand side), gated
@@ -363,9 +406,15 @@ int launch_all(const mpspmv_mat* h, const double* x, int64_t xs, int64_t xoff, d
         MPS_CUDA(cudaGetLastError());
         return MPSPMV_OK;
       }
+      if (!CPLX && !h->d_rowdig) return MPSPMV_EINVAL;  // allocated with the records for real handles
       spmv_runs_wide_kernel<L, CPLX><<<(unsigned)((h->nchunks + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-          m, h->d_xwide, y, ys, h->d_carry, h->carry_k, gate);
+          m, h->d_xwide, y, ys, h->d_carry, h->carry_k, h->d_rowdig, gate);
       MPS_CUDA(cudaGetLastError());
+      if constexpr (!CPLX) {
+        rowdig_finish_kernel<L><<<(unsigned)((h->nrows + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            m, h->d_rowdig, y, ys, h->d_carry, h->carry_k, gate);
+        MPS_CUDA(cudaGetLastError());
+      }
       return launch_combine<L, CPLX>(h, m, y, ys, yoff, k, gate, s);
     }
   }

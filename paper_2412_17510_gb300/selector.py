@@ -5,7 +5,7 @@ Host-side orchestration of C-ABI calls only: features come from
 each precision (``mpspmv_batch_cg``, the method's own solves), training from
 the float32 MLP kernels (``mpspmv_mlp_train``), decisions from
 ``mpspmv_select_precision`` / ``mpspmv_solve_auto`` and the plain ladder
-(``mpspmv_ladder_solve``) stays as fallback and judge.
+(``mpspmv_ladder_solve``) stays as the fallback and the check of the choice.
 
 Classes: 0 binary64, 1 DD, 2 TD, 3 QD, 4 none (QD does not reach the target
 within the iteration cap); a label is the cheapest class whose CG, from

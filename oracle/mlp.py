@@ -4,7 +4,10 @@ A plain numpy float64 multilayer perceptron 32 -> 128 -> 128 -> C with ReLU
 hidden layers and a softmax cross-entropy loss averaged over the batch, its
 analytic backward pass and one plain SGD step.  The GPU trains the same
 network in float32 with its own kernels; tests compare the two and check this
-file against central finite differences and closed forms.
+file against central finite differences and closed forms.  The features are
+standardised before training (per-feature mean and population standard
+deviation over the training rows) and the scaling is then folded into the
+first layer, so that the trained network takes raw features.
 
 Parameter layout (shared in meaning with the CUDA kernels, not in code):
 W1 (32 x 128), b1 (128), W2 (128 x 128), b2 (128), W3 (128 x C), b3 (C),
@@ -75,3 +78,23 @@ def sgd(params, grads, lr):
 
 def predict(params, X):
     return np.argmax(forward(params, X)[-1], axis=1)
+
+
+def standardize(X, eps=1e-6):
+    """Per-feature mean and population standard deviation over the rows of X
+    (float64); a feature whose deviation is below eps keeps the scale 1.
+    Returns mu, sd and the standardised rows (X - mu) / sd."""
+    X = np.asarray(X, dtype=np.float64)
+    mu = X.mean(axis=0)
+    sd = X.std(axis=0)
+    sd = np.where(sd < eps, 1.0, sd)
+    return mu, sd, (X - mu) / sd
+
+
+def fold(params, mu, sd):
+    """The first layer rewritten for raw features:
+    ((x - mu) / sd) W1 + b1 = x (W1 / sd[:, None]) + (b1 - (mu / sd) W1)."""
+    W1, b1 = params[0], params[1]
+    mu = np.asarray(mu, dtype=np.float64)
+    sd = np.asarray(sd, dtype=np.float64)
+    return [W1 / sd[:, None], b1 - (mu / sd) @ W1] + list(params[2:])

@@ -216,10 +216,12 @@ def test_trained_selector_saves_ladder_iterations():
             s.free()
 
 
-def test_standardisation_kernels_match_numpy():
-    """mpspmv_mlp_standardize against a float64 numpy computation, and the
-    fold into W1, b1: the folded network on raw features gives the logits of
-    the unfolded network on standardised features (float tolerance)."""
+def test_standardisation_kernels_match_the_oracle():
+    """mpspmv_mlp_standardize against the oracle's standardisation
+    (oracle/mlp.py, float64), and mpspmv_mlp_fold against the oracle's fold
+    at the kernel's mean and deviation; the folded network on raw features
+    gives the logits of the unfolded network on standardised features (float
+    tolerance)."""
     C = 5
     rng = np.random.default_rng(9)
     n = 300
@@ -232,15 +234,16 @@ def test_standardisation_kernels_match_numpy():
     mps.mpspmv_mlp_standardize(dX, n, mu, sd, Xs)
     torch.cuda.synchronize()
     X64 = X.astype(np.float64)
-    mu_ref = X64.mean(axis=0)
-    sd_ref = X64.std(axis=0)
-    sd_ref[sd_ref < 1e-6] = 1.0
+    mu_ref, sd_ref, _ = omlp.standardize(X64)
     np.testing.assert_allclose(mu.cpu().numpy(), mu_ref, rtol=1e-6, atol=1e-6 * np.abs(X64).max())
     np.testing.assert_allclose(sd.cpu().numpy(), sd_ref, rtol=1e-6)
     assert sd.cpu().numpy()[7] == 1.0
-    xs_ref = (X64 - mu.cpu().numpy().astype(np.float64)) / sd.cpu().numpy().astype(np.float64)
+    mu_k = mu.cpu().numpy().astype(np.float64)
+    sd_k = sd.cpu().numpy().astype(np.float64)
+    xs_ref = (X64 - mu_k) / sd_k  # the oracle's formula at the kernel's float mean and deviation
     np.testing.assert_allclose(Xs.cpu().numpy(), xs_ref, rtol=1e-6, atol=1e-6)
     params = [p.astype(np.float32) for p in omlp.init(C, seed=4)]
+    params[1] = (0.1 * rng.standard_normal(params[1].shape)).astype(np.float32)  # a non-zero b1
     dp = to_dev(flat_params(params))
     lg_std = torch.empty((n, C), dtype=torch.float32, device="cuda")
     mps.mpspmv_mlp_forward(dp, C, Xs, n, lg_std)
@@ -248,5 +251,12 @@ def test_standardisation_kernels_match_numpy():
     lg_raw = torch.empty((n, C), dtype=torch.float32, device="cuda")
     mps.mpspmv_mlp_forward(dp, C, dX, n, lg_raw)
     torch.cuda.synchronize()
+    folded = dp.cpu().numpy()
+    W1f, b1f = folded[:32 * 128].reshape(32, 128), folded[32 * 128:32 * 128 + 128]
+    want = omlp.fold([p.astype(np.float64) for p in params], mu_k, sd_k)
+    np.testing.assert_allclose(W1f, want[0], rtol=1e-6)
+    scale = np.abs(params[1].astype(np.float64)) + np.abs(mu_k / sd_k) @ np.abs(params[0].astype(np.float64))
+    assert np.all(np.abs(b1f - want[1]) <= 1e-6 * scale)
+    assert np.array_equal(folded[32 * 128 + 128:], flat_params(params)[32 * 128 + 128:])  # deeper layers untouched
     a, b = lg_raw.cpu().numpy(), lg_std.cpu().numpy()
     np.testing.assert_allclose(a, b, rtol=1e-3, atol=1e-3 * np.abs(b).max())

@@ -7,6 +7,7 @@ aarch64 alike (gcc's default on aarch64 would otherwise contract).
 """
 import os
 import subprocess
+import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "mporacle.c")
@@ -28,6 +29,8 @@ def build(force=False):
     for p in procs:
         if p.wait() != 0:
             raise RuntimeError("oracle build failed")
+    print("oracle: %s" % ("compiled %d shared libraries with gcc" % len(procs) if procs else "up to date"),
+          file=sys.stderr)
     return outs
 
 

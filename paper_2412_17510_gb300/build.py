@@ -11,6 +11,7 @@ import glob
 import os
 import subprocess
 import sys
+import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -41,7 +42,9 @@ def stale():
 
 def build(force=False, verbose=False):
     if not force and not stale():
+        print("libmpspmv.so: up to date (%s)" % LIB, file=sys.stderr)
         return LIB
+    t0 = time.time()
     os.makedirs(BUILD, exist_ok=True)
     objs, procs = [], []
     for src in sources():
@@ -65,6 +68,8 @@ def build(force=False, verbose=False):
     cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
+    print("libmpspmv.so: compiled %d CUDA translation units for sm_103a and linked in %.1f s (%s)"
+          % (len(objs), time.time() - t0, LIB), file=sys.stderr)
     return LIB
 
 

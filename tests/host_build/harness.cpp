@@ -214,6 +214,20 @@ void flush(const unsigned long long* dp_in, const unsigned long long* dn_in, int
   mpk::fas_to_mp<L, D, 1>(acc, out);
 }
 
+// The flush body on digit arrays of the wide-x row accumulator (D = its
+// digit count for L), as the run kernels and the finishing pass of staged
+// rows call it.
+template <int L>
+void flush_wide(const unsigned long long* dp_in, const unsigned long long* dn_in, int base, double* out) {
+  constexpr int D = mpk::Wide<L>::D;
+  unsigned long long dp[D], dn[D];
+  for (int j = 0; j < D; j++) {
+    dp[j] = dp_in[j];
+    dn[j] = dn_in[j];
+  }
+  mpk::fas_flush_body<L, D, 1>(dp, dn, base, 1, out);
+}
+
 // wide-x form: the record of one column part, and a row of n entries (a[i]
 // binary64, X + i L the components of the x it multiplies) summed in the
 // row accumulator of that form and cut to L components
@@ -380,6 +394,15 @@ int host_flush(int L, const unsigned long long* dp, const unsigned long long* dn
     case 2: flush<2>(dp, dn, base, out); return 0;
     case 3: flush<3>(dp, dn, base, out); return 0;
     case 4: flush<4>(dp, dn, base, out); return 0;
+    default: return -1;
+  }
+}
+
+int host_flush_wide(int L, const unsigned long long* dp, const unsigned long long* dn, int base, double* out) {
+  switch (L) {
+    case 2: flush_wide<2>(dp, dn, base, out); return 0;
+    case 3: flush_wide<3>(dp, dn, base, out); return 0;
+    case 4: flush_wide<4>(dp, dn, base, out); return 0;
     default: return -1;
   }
 }

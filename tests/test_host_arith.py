@@ -69,6 +69,7 @@ def lib(tmp_path_factory):
     h.host_entry_sum.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
     _up = ctypes.POINTER(ctypes.c_ulonglong)
     h.host_flush.argtypes = [ctypes.c_int, _up, _up, ctypes.c_int, _dp]
+    h.host_flush_wide.argtypes = [ctypes.c_int, _up, _up, ctypes.c_int, _dp]
     h.host_row_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
     h.host_row_sum_c.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
     h.host_axpy_elem.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
@@ -354,6 +355,41 @@ def test_flush_of_random_digit_arrays(lib, L):
         assert shift >= 0
         want = _cut(V << shift, L)
         assert np.array_equal(out, want), (L, case)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+def test_staged_digit_differences_flush_like_the_accumulator(lib, L):
+    """The finishing pass of staged rows flushes the digit differences
+    dp_j - dn_j, stored as 64-bit two's complement words, with the negative
+    digits zero, where the run kernel flushed the pair (dp, dn) itself
+    (wide-x row accumulator, D digits).  Both give the same components, and
+    both are the exact value sum_j (dp_j - dn_j) 2^(32 j + base) cut to L
+    components: random digit contents of either sign, and rows whose digits
+    cancel to zero."""
+    D = lib.host_wide_digits(L)
+    rng = np.random.default_rng(900 + L)
+    up = ctypes.POINTER(ctypes.c_ulonglong)
+    zeros = np.zeros(D, dtype=np.uint64)
+    for case in range(3000):
+        dp = rng.integers(0, 2 ** 62, D, dtype=np.uint64) >> rng.integers(0, 62, D).astype(np.uint64)
+        dn = rng.integers(0, 2 ** 62, D, dtype=np.uint64) >> rng.integers(0, 62, D).astype(np.uint64)
+        dp[rng.random(D) < 0.2] = 0
+        dn[rng.random(D) < 0.2] = 0
+        if case % 10 == 0:
+            dn = dp.copy()  # a row that cancels exactly
+        dp[D - 1] >>= np.uint64(34)  # keep |value| below 2^(32 D - 2)
+        dn[D - 1] >>= np.uint64(34)
+        base = int(rng.integers(-1300, 1020 - 32 * D))  # the value stays inside the binary64 range
+        pair, staged = np.zeros(L), np.zeros(L)
+        dpc, dnc = np.ascontiguousarray(dp), np.ascontiguousarray(dn)
+        lib.host_flush_wide(L, dpc.ctypes.data_as(up), dnc.ctypes.data_as(up), base, _d(pair))
+        diff = np.ascontiguousarray(np.subtract(dp, dn))  # wraps modulo 2^64: the two's complement word
+        lib.host_flush_wide(L, diff.ctypes.data_as(up), zeros.ctypes.data_as(up), base, _d(staged))
+        assert np.array_equal(pair, staged), (L, case)
+        V = sum((int(a) - int(b)) << (32 * j) for j, (a, b) in enumerate(zip(dp, dn)))
+        shift = base + SC
+        assert shift >= 0
+        assert np.array_equal(pair, _cut(V << shift, L)), (L, case)
 
 
 @pytest.mark.parametrize("L", [2, 3, 4])

@@ -63,7 +63,13 @@ typedef enum { MPSPMV_D = 1, MPSPMV_DD = 2, MPSPMV_TD = 3, MPSPMV_QD = 4 } mpspm
                                 truncation.  Krylov vector updates and inner products on such a handle
                                 are exact in the same way.  Same bound 8 m u (|A||x|)_i, error of the
                                 same order; results are not bit-identical to the paper-order
-                                arithmetic. */
+                                arithmetic.  Single-vector products on such handles whose values are
+                                binary64 (one stored value plane) first turn x, per product, into one
+                                fixed-point number per column (x truncated toward zero to a 4 / 5 / 7
+                                word mantissa for DD / TD / QD), so each stored entry is one integer
+                                product; the handle then holds 32 bytes per column part for these
+                                records and, for real matrices summed over runs, 96 bytes per row for
+                                finished row sums that a second pass turns into components. */
 #define MPSPMV_TRANSPOSE 32u /* also build A^T (a second internal matrix from the swapped triplets, about
                                 doubling the device bytes) for mpspmv_spmtv and mpspmv_bicg */
 
